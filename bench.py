@@ -1,0 +1,340 @@
+"""Benchmark of the operator-split tissue SSA on GB300.
+
+One "step" is one Lie splitting step of the whole hot path (chi on every
+cell, then S on every x-face and every y-face) over the benchmark tissue:
+64x64 cells of 16x16 voxels, the Notch-Delta model, dt = 0.1 (the medium
+tissue; synthetic, seeded).  The state is first advanced by an untimed
+burn-in so that the timed steps see molecule counts near their working
+level, then W warm-up steps and K timed steps run.
+
+Metric: SSA events per second (all events of chi and both face phases), with
+cell-steps per second beside it.  `value` times the steps with the state
+resident in device memory (CUDA events on the tissue's stream, L2 flushed
+between steps); `e2e` times the same steps through the C ABI with the state
+copied host->device before and device->host after every step.
+
+Multi-GPU (torchrun, N ranks): every rank advances its own replica tissue
+(tissue_id = rank); there is no data exchange (weak scaling).
+
+`--impl reference` times the CPU oracle (test infrastructure, plain C with
+OpenMP) on a bounded patch of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1806_10889_gb300 import workloads as W  # noqa: E402
+
+METRIC = "SSA events/s (chi + face binding), medium tissue 64x64 cells x 16x16 voxels, dt 0.1"
+UNIT = "events/s"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Issue-slot peak of the chip: 152 SMs x 4 schedulers x 1 warp-instruction per
+# clock at the 2070 MHz maximum SM clock.
+ISSUE_PEAK_GINST = 152 * 4 * 2.070
+# Warp instructions the chi kernel executes per chi event on this workload,
+# from ncu (smsp__inst_executed.sum / events; profiles/chi_medium_ncu.md).
+CHI_INST_PER_EVENT = None
+# Algorithmic DRAM bytes of one chi launch per cell: the state read + write.
+STATE_BYTES_PER_CELL_RW = lambda V: 2 * 3 * V * 4  # noqa: E731
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(PEAKS) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1806_10889_gb300.tissue import DEFAULT_CHI_WPB, Tissue
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    run = W.medium(args.dt)
+    spec = run.tissue
+    if world > 1:  # independent replica per rank
+        from dataclasses import replace
+        spec = replace(spec, tissue_id=rank)
+    g = Tissue(spec)
+    g.set_launch(args.chi_wpb or DEFAULT_CHI_WPB)
+    burn = int(round(args.burn_in / args.dt))
+    if burn:
+        g.step(args.dt, burn)
+    for _ in range(args.warmup):
+        g.step(args.dt, 1)
+    g.sync()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    ev0 = g.total_events()
+    chi_ms = sig_ms = 0.0
+    step_ms = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clocks:
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the event pair)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c_ms, s_ms = g.step_timed(args.dt, 1)
+            b.record(stream)
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+            chi_ms += c_ms
+            sig_ms += s_ms
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+    ev1 = g.total_events()
+    events = int((ev1 - ev0).sum())
+    chi_events = int(ev1[0] - ev0[0])
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms, float(events)], device="cuda", dtype=torch.float64)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_ms_job, events_job = float(mx[0]), float(sm[1])
+    else:
+        total_ms_job, events_job = total_ms, float(events)
+    value = events_job / (total_ms_job / 1e3)
+    cell_steps = spec.cells * args.steps * world
+
+    # end to end through the C ABI: pinned host state in and out every step
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(spec.state_ints, dtype=torch.int32, pin_memory=True)
+        g.read_counts_into(host)
+        e0 = g.total_events()
+        k0 = g.get_step()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            g.write_counts_from(host, step_index=k0 + i)   # H2D of the step's input state
+            g.step(args.dt, 1)
+            g.read_counts_into(host)                       # D2H of the step's result
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e_ev = float((g.total_events() - e0).sum())
+        if dist:
+            t = torch.tensor([e2e_s, e_ev], device="cuda", dtype=torch.float64)
+            mx = t.clone()
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+            sm = t.clone()
+            dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+            e2e_s, e_ev = float(mx[0]), float(sm[1])
+        nbytes = spec.state_ints * 4
+        e2e = {"value": e_ev / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+
+    peaks, peak_kind = _peaks()
+    chi_s = chi_ms / 1e3
+    chi_rate = chi_events / chi_s if chi_s > 0 else 0.0
+    hbm_achieved = STATE_BYTES_PER_CELL_RW(spec.V) * spec.cells * args.steps / chi_s / 1e9
+    if CHI_INST_PER_EVENT:
+        ach = chi_rate * CHI_INST_PER_EVENT / 1e9
+        roofline = {"bound": "alu", "achieved": ach, "peak": ISSUE_PEAK_GINST,
+                    "unit": "Gwarp-inst/s", "frac": ach / ISSUE_PEAK_GINST,
+                    "traffic": args.chi_traffic,
+                    "kernel": "k_chi", "inst_per_event": CHI_INST_PER_EVENT,
+                    "hbm_gbs": hbm_achieved, "hbm_frac": hbm_achieved / peaks["hbm_gbs"],
+                    "peak_source": "152 SMs x 4 issue/clk x 2.070 GHz"}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": hbm_achieved / peaks["hbm_gbs"],
+                    "traffic": args.chi_traffic, "kernel": "k_chi",
+                    "peak_source": f"{peak_kind} hbm_gbs"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_job / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
+        "data": "synthetic", "impl": "ours",
+        "config": {"workload": "medium tissue 64x64 cells of 16x16 voxels, Notch-Delta model",
+                   "dt": args.dt, "burn_in_time": args.burn_in, "cells": spec.cells,
+                   "voxels_per_cell": spec.V, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}", "chi_warps_per_block":
+                   args.chi_wpb or DEFAULT_CHI_WPB},
+        "cell_steps_per_s": cell_steps / (total_ms_job / 1e3),
+        "events_per_step": events_job / args.steps,
+        "chi_ms_per_step": chi_ms / args.steps, "sig_ms_per_step": sig_ms / args.steps,
+        "e2e": e2e,
+        "gpu_launches": 4 * args.steps,
+        "roofline": roofline,
+        "clocks": clocks.summary(),
+        "wall_s_timed": wall,
+    }
+    g.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def _oracle_patch(side: int):
+    import oracle as O
+    spec = W.medium(0.1).tissue
+    d = O.Desc(side, side, spec.n, seed=spec.seed, tissue_id=spec.tissue_id,
+               init_lambda=tuple(spec.init_lambda))
+    return O, d, O.Model(**spec.model)
+
+
+def cpu_baseline(args, side: int = 64, steps: int = 4):
+    """The oracle, as it stands, on a bounded patch of the benchmark tissue."""
+    O, d, m = _oracle_patch(side)
+    counts = O.init_counts(d)
+    threads = O.max_threads()
+    total = 0
+    t0 = time.perf_counter()
+    for k in range(steps):
+        ne, _ = O.step(d, m, counts, k, 1, args.dt, n_threads=threads)
+        total += int(ne.sum())
+    dt_s = time.perf_counter() - t0
+    return {"value": total / dt_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{side}x{side} cells of the medium tissue (16x16 voxels), steps 0-{steps - 1} "
+                      f"from the initial state, dt {args.dt}, {total} events in {dt_s:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    O, d, m = _oracle_patch(args.ref_side)
+    counts = O.init_counts(d)
+    threads = O.max_threads()
+    for k in range(args.warmup):
+        O.step(d, m, counts, k, 1, args.dt, n_threads=threads)
+    total, t0 = 0, time.perf_counter()
+    for k in range(args.warmup, args.warmup + args.steps):
+        ne, _ = O.step(d, m, counts, k, 1, args.dt, n_threads=threads)
+        total += int(ne.sum())
+    el = time.perf_counter() - t0
+    value = total / el
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "medium tissue 64x64 cells of 16x16 voxels, Notch-Delta model",
+                       "dt": args.dt, "sample_cells": args.ref_side ** 2},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{args.ref_side}x{args.ref_side}-cell patch per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--dt", type=float, default=0.1, choices=[0.01, 0.1, 1.0])
+    ap.add_argument("--burn-in", type=float, default=20.0, help="untimed simulated time first")
+    ap.add_argument("--chi-wpb", type=int, default=0)
+    ap.add_argument("--chi-traffic", type=float, default=None,
+                    help="DRAM bytes per chi launch from an ncu capture, if known")
+    ap.add_argument("--ref-side", type=int, default=16)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    rank, world, local_rank = _env_rank()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,154 @@
+/*
+ * tissue.h -- C ABI of the GB300 operator-split tissue SSA (libtissue.so).
+ *
+ * The method (arXiv 1806.10889, "Orchestral"):
+ *   A tissue is a layer of identical cells, each with at most four neighbours
+ *   (Sec. III-A1).  Time advances by Lie operator splitting (Sec. II; Fig. 1):
+ *   in every step of length dt the intracellular module chi advances every
+ *   cell independently (Sec. II-A1), then the signalling module S advances
+ *   every pair of neighbouring cells independently (Sec. II-A2).  The
+ *   translations T_{chi->S} and T_{S->chi} (Sec. II-B) gather a face's
+ *   boundary voxels from the two cells and write the result back.  Every
+ *   module call runs on its own clock over [0, dt) (the per-cell "end_time"
+ *   of the network file, Fig. 2) and draws from its own seeded stream
+ *   (the "-seed" of the module command lines, Fig. 3).
+ *
+ *   chi here is a lattice RDME on an n x n voxel grid solved by the exact
+ *   direct-method SSA; S is Delta-Notch binding across a shared face, with
+ *   every boundary voxel coupled to a single face (Sec. III-A1), realised as
+ *   an x-face phase followed by a y-face phase.
+ *
+ * State layout (device memory, owned by the caller):
+ *   int32 counts[cell][species][voxel], species D = 0, N = 1, R = 2,
+ *   cell c = cy * width + cx, voxel v = vy * n + vx.
+ *   tissue_state_bytes() gives its size.  The base must be 16-byte aligned.
+ *
+ * Arithmetic contract (exactly reproducible; the CPU oracle defines it):
+ *   - Philox4x32-10, key = seed, counter = (event, step, unit,
+ *     tissue_id | tag << 24) with tag 1 = chi, 2 = x-face, 3 = y-face,
+ *     4 = initial counts.
+ *   - Propensities are integers in units of 2^-32 per unit time; a rate x is
+ *     quantised once as round-half-even(x * 2^32).
+ *   - Event times are IEEE binary64: tau = E / (A * 2^-32) with E the
+ *     fixed-point -ln(u1); an event fires iff t + tau < dt.
+ *
+ * Threading: a tissue handle is not thread-safe; use one handle per host
+ * thread.  All device work is ordered on the stream given at creation.
+ *
+ * Errors: every int-returning call returns TISSUE_OK (0) or a negative
+ * TISSUE_E_* code; nothing is thrown across the ABI.  Device-side errors
+ * (count or propensity overflow) are latched in a device flag and reported
+ * by the next synchronising call (tissue_read_counts, tissue_read_stats,
+ * tissue_total_events, tissue_sync).
+ */
+#ifndef TISSUE_H
+#define TISSUE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TISSUE_OK 0
+#define TISSUE_E_ARG (-1)      /* invalid argument (sizes, ranges, null pointers) */
+#define TISSUE_E_NOMEM (-2)    /* library scratch allocation failed */
+#define TISSUE_E_NOMODEL (-3)  /* tissue_step before tissue_set_model */
+#define TISSUE_E_OVERFLOW (-4) /* a count passed 2^30-1 or a propensity reached 2^52 */
+#define TISSUE_E_CUDA (-5)     /* a CUDA runtime call failed */
+#define TISSUE_E_TIMEOUT (-6)  /* a bounded device wait gave up */
+#define TISSUE_E_BUDGET (-7)   /* admission refused: memory budget exceeded */
+
+#define TISSUE_COUNT_MAX ((1 << 30) - 1)
+
+typedef struct tissue tissue; /* opaque, library-owned */
+
+typedef struct {
+  uint32_t width, height; /* cells; the tissue is width x height, not periodic; >= 1 each */
+  uint32_t n;             /* voxels per cell side, 2..32 (V = n*n voxels per cell) */
+  uint32_t tissue_id;     /* < 2^24; part of every Philox counter */
+  uint64_t seed;          /* Philox key */
+  double init_lambda[3];  /* Poisson mean of the initial D, N, R count per voxel, 0..700 */
+} tissue_desc;
+
+/* Rates (all finite, >= 0 and < 2^20; K > 0).  Per voxel:
+ *   D production kD / (1 + (R/K)^2)      N production kN
+ *   decay gD*D, gN*N, gR*R
+ *   hop of each molecule to each existing neighbour voxel at hopD, hopN, hopR
+ *   D + N -> R at k_in*D*N and R -> D + N at k_off*R (in-voxel; 0 in the tissue model)
+ * Across a face, for every voxel pair (i in one cell, j in the other):
+ *   D(i) + N(j) -> R(j) at k_bind*D(i)*N(j), in both directions. */
+typedef struct {
+  double kD, K, kN, gD, gN, gR, hopD, hopN, hopR, k_in, k_off, k_bind;
+} tissue_model;
+
+/* Bytes of the caller-owned state buffer: width*height*3*n*n*4.
+ * Returns 0 for an invalid descriptor. */
+size_t tissue_state_bytes(const tissue_desc* desc);
+
+/* Bytes the library itself allocates for one tissue (statistics, flags,
+ * tables), for memory-budget admission.  0 for an invalid descriptor. */
+size_t tissue_scratch_bytes(const tissue_desc* desc);
+
+/* Bind a tissue to a caller-owned device buffer (>= tissue_state_bytes,
+ * 16-byte aligned) and a CUDA stream (NULL = legacy default stream), and
+ * enqueue the Poisson initial counts (Sec. III-A1 tissue; per-cell seeds of
+ * Fig. 2).  The buffer must outlive the handle.  On success *out receives the
+ * handle and the global step index is 0. */
+int tissue_create(const tissue_desc* desc, void* dev_counts, size_t bytes, void* cuda_stream,
+                  tissue** out);
+
+/* Set (or replace, between steps) the model; the rates are copied. */
+int tissue_set_model(tissue* t, const tissue_model* model);
+
+/* Overwrite the state from host memory (n int32 values, exactly
+ * width*height*3*V) and set the global step index (checkpoint resume).
+ * Synchronises the stream.  Clears the device error flag. */
+int tissue_write_counts(tissue* t, const int32_t* host, size_t n, uint32_t step_index);
+
+/* Enqueue n_steps splitting steps of length dt (> 0, finite): for each step
+ * k, chi on every cell, S on every x-face, then S on every y-face.
+ * Asynchronous on the tissue's stream; advances the global step index. */
+int tissue_step(tissue* t, double dt, uint32_t n_steps);
+
+/* As tissue_step, but also measures the device time of each phase with CUDA
+ * events recorded on the tissue's stream around every launch, and waits for
+ * the work to finish.  ms_chi receives the summed duration of the chi
+ * launches, ms_sig that of the two face phases (either may be NULL). */
+int tissue_step_timed(tissue* t, double dt, uint32_t n_steps, double* ms_chi, double* ms_sig);
+
+/* Copy the state to host memory (n int32 values) after the queued work;
+ * synchronises the stream and reports a latched device error. */
+int tissue_read_counts(tissue* t, int32_t* host, size_t n);
+
+/* Statistics of the LAST step, each laid out [3][cells]: row 0 chi of the
+ * cell, row 1 the x-face the cell owns (its +x face), row 2 its y-face
+ * (0 where the cell owns no such face).  n_events: fired events; t_last:
+ * local time of the last fired event (0.0 if none).  n = 3*cells.
+ * Either pointer may be NULL.  Synchronises. */
+int tissue_read_stats(tissue* t, uint64_t* n_events, double* t_last, size_t n);
+
+/* Events fired since creation: out[0] chi, out[1] x-faces, out[2] y-faces.
+ * Synchronises. */
+int tissue_total_events(tissue* t, uint64_t out[3]);
+
+/* Global step index (the next step to run). */
+int tissue_get_step(const tissue* t, uint32_t* step_index);
+
+/* Wait for the queued work; report a latched device error. */
+int tissue_sync(tissue* t);
+
+/* Launch shape of the chi kernel: warps (cells) per block, 1..16.
+ * Results never depend on it. */
+int tissue_set_launch(tissue* t, uint32_t chi_warps_per_block);
+
+/* Release library scratch (not the caller's buffer or stream). */
+void tissue_destroy(tissue* t);
+
+const char* tissue_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -19,6 +19,7 @@ from .oracle import (  # noqa: F401
     quantize,
     hill_q,
     init_counts,
+    init_cell,
     chi_cell,
     sig_face,
     step,

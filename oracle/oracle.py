@@ -142,6 +142,8 @@ def lib():
             L.orc_validate.restype = C.c_int
             L.orc_init_counts.argtypes = [P(_Desc), C.c_void_p]
             L.orc_init_counts.restype = C.c_int
+            L.orc_init_cell.argtypes = [P(_Desc), C.c_void_p, C.c_uint32]
+            L.orc_init_cell.restype = C.c_int
             L.orc_chi_cell.argtypes = [P(_Desc), P(_Model), C.c_void_p, C.c_uint32, C.c_uint32,
                                        C.c_double, P(C.c_uint64), P(C.c_double), C.c_void_p,
                                        C.c_size_t, P(C.c_size_t)]
@@ -218,6 +220,15 @@ def init_counts(d: Desc) -> np.ndarray:
     if rc:
         raise OracleError(rc, "init_counts")
     return counts
+
+
+def init_cell(d: Desc, counts: np.ndarray, c: int) -> None:
+    """Write the initial counts of cell c only into a full-tissue array."""
+    _check_state(d, counts)
+    dc = d.to_c()
+    rc = lib().orc_init_cell(C.byref(dc), _ptr(counts), int(c))
+    if rc:
+        raise OracleError(rc, "init_cell")
 
 
 def chi_cell(d: Desc, m: Model, counts: np.ndarray, c: int, step: int, dt: float,

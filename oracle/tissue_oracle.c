@@ -278,6 +278,35 @@ static void record(orc_event* trace, size_t cap, size_t* len, uint32_t step, uin
 /* Initial state: Poisson(lambda_s) per voxel and species, by inversion of    */
 /* the CDF accumulated term by term, p_k = p_{k-1} * lambda / k.              */
 /* ------------------------------------------------------------------------ */
+static int32_t poisson_voxel(const orc_desc* d, double lam, double p0, uint32_t c, int s, int v) {
+  uint32_t w[4];
+  draw(d, (uint32_t)v, (uint32_t)s, c, d->tissue_id | (ORC_TAG_INIT << 24), w);
+  double u = (double)((((uint64_t)w[1] << 32) | w[0]) >> 11) * 0x1p-53;
+  int k = 0;
+  double p = p0, F = p0;
+  while (u >= F && k < 4096) {
+    k += 1;
+    p = (p * lam) / (double)k;
+    F = F + p;
+  }
+  return k;
+}
+
+/* Initial counts of one cell c only (the other cells are left untouched). */
+int orc_init_cell(const orc_desc* d, int32_t* counts, uint32_t c) {
+  int rc = orc_validate(d, NULL);
+  if (rc) return rc;
+  if ((uint64_t)c >= (uint64_t)d->width * d->height) return ORC_E_ARG;
+  const int V = (int)(d->n * d->n);
+  for (int s = 0; s < 3; ++s) {
+    const double lam = d->init_lambda[s] + (g_mutation == 4 ? 0.5 : 0.0);
+    const double p0 = exp(-lam);
+    for (int v = 0; v < V; ++v)
+      counts[((int64_t)c * 3 + s) * V + v] = poisson_voxel(d, lam, p0, c, s, v);
+  }
+  return ORC_OK;
+}
+
 int orc_init_counts(const orc_desc* d, int32_t* counts) {
   int rc = orc_validate(d, NULL);
   if (rc) return rc;
@@ -287,19 +316,8 @@ int orc_init_counts(const orc_desc* d, int32_t* counts) {
     const double lam = d->init_lambda[s] + (g_mutation == 4 ? 0.5 : 0.0);
     const double p0 = exp(-lam);
     for (int64_t c = 0; c < cells; ++c) {
-      for (int v = 0; v < V; ++v) {
-        uint32_t w[4];
-        draw(d, (uint32_t)v, (uint32_t)s, (uint32_t)c, d->tissue_id | (ORC_TAG_INIT << 24), w);
-        double u = (double)((((uint64_t)w[1] << 32) | w[0]) >> 11) * 0x1p-53;
-        int k = 0;
-        double p = p0, F = p0;
-        while (u >= F && k < 4096) {
-          k += 1;
-          p = (p * lam) / (double)k;
-          F = F + p;
-        }
-        counts[(c * 3 + s) * V + v] = k;
-      }
+      for (int v = 0; v < V; ++v)
+        counts[(c * 3 + s) * V + v] = poisson_voxel(d, lam, p0, (uint32_t)c, s, v);
     }
   }
   return ORC_OK;

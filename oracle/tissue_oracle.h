@@ -85,6 +85,7 @@ int orc_hill_q(const orc_model* m, int64_t R, uint64_t* q);
 int orc_validate(const orc_desc* d, const orc_model* m);
 
 int orc_init_counts(const orc_desc* d, int32_t* counts);
+int orc_init_cell(const orc_desc* d, int32_t* counts, uint32_t c);
 int orc_chi_cell(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_t c,
                  uint32_t step, double dt, uint64_t* n_events, double* t_last,
                  orc_event* trace, size_t trace_cap, size_t* trace_len);

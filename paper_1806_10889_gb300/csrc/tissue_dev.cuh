@@ -1,0 +1,125 @@
+// Device building blocks of the tissue SSA (sm_103a).
+//
+// Counter-based random numbers, the fixed-point exponential variate, integer
+// propensities with exact overflow detection, and warp-level helpers.  All
+// arithmetic here is exact integer arithmetic or single IEEE binary64
+// operations through the _rn intrinsics, so the results are reproducible bit
+// for bit on any IEEE machine.
+#pragma once
+#include <cstdint>
+
+#include "tissue_internal.h"
+
+namespace tsg {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplications whose high words are xored into the other
+// counter words with the round key; the key advances by the golden-ratio and
+// sqrt(3)-1 Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                       uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// ---------------------------------------------------------------------------
+// -ln(k * 2^-53) * 2^58 for k in [1, 2^53], in integer arithmetic.
+// Write k = 2^j m, m in [1,2).  With h = (m-1)/2 (m <= sqrt 2) or
+// h = (2-m)/4 (m > sqrt 2, one more power of two), ln of the mantissa part is
+// +-2 atanh(h / (1 +- h)) (Abramowitz & Stegun 4.1.27).  1/(1 +- h) comes from
+// four Newton-Raphson steps y <- y (2 - d y) started at 2 - d; atanh(s)/s is
+// the series sum_{i<=11} s^{2i} / (2i+1) evaluated by Horner's rule.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t mul_q62(uint64_t a, uint64_t b) {
+  return (__umul64hi(a, b) << 2) | ((a * b) >> 62);
+}
+
+// round(2^63 / (2i + 1)); never a tie since 2i + 1 > 1 is odd.
+__host__ __device__ constexpr uint64_t atanh_coef(int i) {
+  return (0x8000000000000000ull + static_cast<uint64_t>(i)) / (2ull * i + 1ull);
+}
+
+__device__ __forceinline__ uint64_t neg_ln_q58(uint64_t k) {
+  const int lz = __clzll(static_cast<long long>(k));
+  const uint64_t m = k << lz;  // Q1.63
+  const bool upper = m > 0xB504F333F9DE6484ull;  // floor(sqrt 2 * 2^63)
+  const uint64_t h = upper ? ((0ull - m) >> 1) : (m - 0x8000000000000000ull);
+  const uint64_t d = upper ? (0x4000000000000000ull - (h >> 2)) : (0x4000000000000000ull + (h >> 2));
+  uint64_t y = 0x8000000000000000ull - d;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) y = mul_q62(y, 0x8000000000000000ull - mul_q62(d, y));
+  const uint64_t s = mul_q62(h, y);
+  const uint64_t z = __umul64hi(s, s);
+  constexpr uint64_t kC[12] = {atanh_coef(0), atanh_coef(1), atanh_coef(2),  atanh_coef(3),
+                               atanh_coef(4), atanh_coef(5), atanh_coef(6),  atanh_coef(7),
+                               atanh_coef(8), atanh_coef(9), atanh_coef(10), atanh_coef(11)};
+  uint64_t p = kC[11];
+#pragma unroll
+  for (int i = 10; i >= 0; --i) p = __umul64hi(p, z) + kC[i];
+  const uint64_t two_atanh = mul_q62(s, p);
+  const uint64_t nln2 = static_cast<uint64_t>(upper ? 52 - (63 - lz) : 53 - (63 - lz));
+  constexpr uint64_t kLn2Q64 = 0xB17217F7D1CF79ACull;  // round(ln 2 * 2^64)
+  uint64_t lo = nln2 * kLn2Q64, hi = __umul64hi(nln2, kLn2Q64);
+  if (upper) {
+    const uint64_t t = lo + two_atanh;
+    hi += (t < lo);
+    lo = t;
+  } else {
+    hi -= (lo < two_atanh);
+    lo -= two_atanh;
+  }
+  return (hi << 58) | (lo >> 6);
+}
+
+// Unit-mean exponential from Philox words 0,1: u1 = (bits53 + 1) 2^-53.
+__device__ __forceinline__ double exp_variate(uint32_t w0, uint32_t w1) {
+  const uint64_t bits = ((static_cast<uint64_t>(w1) << 32) | w0) >> 11;
+  return __dmul_rn(__ull2double_rn(neg_ln_q58(bits + 1)), 0x1p-58);
+}
+
+// ---------------------------------------------------------------------------
+// Integer propensities.  a*x is exact; the flag records whether the exact
+// product reached 2^52 (the per-voxel / per-channel limit).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t mul_lim(uint64_t a, uint64_t x, bool& ovf) {
+  const uint64_t lo = a * x;
+  ovf |= (__umul64hi(a, x) != 0ull) | ((lo >> 52) != 0ull);
+  return lo;
+}
+
+// Hill-repressed Delta production kD / (1 + (R/K)^2), binary64, quantised.
+__device__ __forceinline__ uint64_t hill_direct(const QRates& q, uint32_t R) {
+  const double x = __ddiv_rn(static_cast<double>(R), q.K);
+  const double den = __dadd_rn(1.0, __dmul_rn(x, x));
+  return __double2ull_rn(__dmul_rn(__ddiv_rn(q.kD, den), 4294967296.0));
+}
+
+__device__ __forceinline__ uint64_t hill_q(const QRates& q, uint32_t R) {
+  return R < kHillTab ? __ldg(q.hill + R) : hill_direct(q, R);
+}
+
+// v / n for v < 1024, n <= 32: (v * ceil(2^16 / n)) >> 16 is exact there.
+__device__ __forceinline__ int div_n(int v, uint32_t magic) {
+  return static_cast<int>((static_cast<uint32_t>(v) * magic) >> 16);
+}
+
+}  // namespace tsg

@@ -1,0 +1,51 @@
+// Internal declarations shared by the CUDA translation units of libtissue.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace tsg {
+
+constexpr uint32_t kTagChi = 1u, kTagSx = 2u, kTagSy = 3u, kTagInit = 4u;
+constexpr uint32_t kHillTab = 4096;  // tabulated Hill production for R < kHillTab
+constexpr int kErrOverflow = 1;
+constexpr int kErrEventIndex = 2;
+constexpr int kErrInternal = 4;  // a selection invariant failed (never expected)
+constexpr int kCountMax = (1 << 30) - 1;      // largest count a voxel may hold
+constexpr uint64_t kPropLimit = 1ull << 52;  // a voxel or face channel must stay below
+
+// Quantised model: every rate as an integer in units of 2^-32 per unit time.
+struct QRates {
+  uint64_t kN, gD, gN, gR, hopD, hopN, hopR, k_in, k_off, k_bind;
+  uint64_t cD[5], cN[5], cR[5];  // g + nn * hop for nn existing neighbours
+  double kD, K;
+  const uint64_t* hill;  // device table, kHillTab entries
+};
+
+// One tissue as the kernels see it.
+struct TissueView {
+  int32_t* counts;      // [cell][3][V]
+  uint32_t width, height, n, V;
+  uint32_t magic;       // ceil(2^16 / n)
+  uint32_t tissue_id;
+  uint64_t seed;
+  QRates q;
+  uint64_t* ev_last;    // [3][cells] events of the last step
+  double* t_last;       // [3][cells] time of the last event of the last step
+  uint64_t* ev_total;   // [3][cells] events since creation
+  const uint32_t* step; // device step counter
+  int* err;             // device error flag (bit mask)
+};
+
+// Launchers (enqueue on `stream`; return the launch error).
+cudaError_t launch_hill_table(const QRates& q, uint64_t* table, cudaStream_t stream);
+cudaError_t launch_init(const TissueView& t, const double p0[3], const double lam[3],
+                        cudaStream_t stream);
+cudaError_t launch_chi(const TissueView& t, uint32_t step_off, double dt, int warps_per_block,
+                       cudaStream_t stream);
+cudaError_t launch_sig(const TissueView& t, int axis, uint32_t step_off, double dt,
+                       cudaStream_t stream);
+cudaError_t launch_step_advance(uint32_t* step, uint32_t n, cudaStream_t stream);
+
+}  // namespace tsg

@@ -1,0 +1,351 @@
+// libtissue: the C ABI of include/tissue.h.
+//
+// The orchestration role of the paper's Dask DAG (Sec. II-C, Fig. 4) is taken
+// by stream order: each splitting step enqueues K_chi over all cells, then
+// K_sig over the x-faces, then over the y-faces, on the tissue's stream.  The
+// state never leaves device memory between steps (the paper's per-module
+// input/output files become in-place reads and writes of one array).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tissue.h"
+#include "tissue_internal.h"
+
+using namespace tsg;
+
+struct tissue {
+  tissue_desc d{};
+  int32_t* counts = nullptr;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  bool has_model = false;
+  QRates q{};
+  unsigned char* scratch = nullptr;
+  uint64_t* hill = nullptr;
+  uint64_t* ev_last = nullptr;
+  double* t_last = nullptr;
+  uint64_t* ev_total = nullptr;
+  uint32_t* d_step = nullptr;
+  int* d_err = nullptr;
+  uint32_t step_index = 0;
+  int chi_wpb = 4;
+};
+
+namespace {
+
+bool desc_ok(const tissue_desc* d) {
+  if (!d) return false;
+  if (d->width < 1 || d->height < 1 || d->n < 2 || d->n > 32) return false;
+  if (d->tissue_id >= (1u << 24)) return false;
+  if (static_cast<uint64_t>(d->width) * d->height > 0xFFFFFFFFull) return false;
+  for (int s = 0; s < 3; ++s)
+    if (!(d->init_lambda[s] >= 0.0 && d->init_lambda[s] <= 700.0)) return false;
+  return true;
+}
+
+uint64_t cells_of(const tissue_desc* d) { return static_cast<uint64_t>(d->width) * d->height; }
+
+struct ScratchLayout {
+  size_t hill, ev_last, t_last, ev_total, step, err, total;
+};
+
+ScratchLayout layout(const tissue_desc* d) {
+  const size_t cells = cells_of(d);
+  auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
+  ScratchLayout L{};
+  size_t o = 0;
+  L.hill = o;
+  o = up(o + sizeof(uint64_t) * kHillTab);
+  L.ev_last = o;
+  o = up(o + sizeof(uint64_t) * 3 * cells);
+  L.t_last = o;
+  o = up(o + sizeof(double) * 3 * cells);
+  L.ev_total = o;
+  o = up(o + sizeof(uint64_t) * 3 * cells);
+  L.step = o;
+  o = up(o + sizeof(uint32_t));
+  L.err = o;
+  o = up(o + sizeof(int));
+  L.total = o;
+  return L;
+}
+
+bool rate_ok(double x) { return std::isfinite(x) && x >= 0.0 && x < 1048576.0; }
+
+// Rate x as an integer number of 2^-32 units: round-half-even(x * 2^32).
+uint64_t quantise(double x) { return static_cast<uint64_t>(std::nearbyint(x * 4294967296.0)); }
+
+TissueView view_of(const tissue* t) {
+  TissueView v{};
+  v.counts = t->counts;
+  v.width = t->d.width;
+  v.height = t->d.height;
+  v.n = t->d.n;
+  v.V = t->d.n * t->d.n;
+  v.magic = (65536u + t->d.n - 1) / t->d.n;
+  v.tissue_id = t->d.tissue_id;
+  v.seed = t->d.seed;
+  v.q = t->q;
+  v.ev_last = t->ev_last;
+  v.t_last = t->t_last;
+  v.ev_total = t->ev_total;
+  v.step = t->d_step;
+  v.err = t->d_err;
+  return v;
+}
+
+int device_error(tissue* t) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, t->d_err, sizeof(int), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  if (cudaStreamSynchronize(t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  if (h & kErrInternal) return TISSUE_E_CUDA;
+  return h ? TISSUE_E_OVERFLOW : TISSUE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tissue_state_bytes(const tissue_desc* d) {
+  if (!desc_ok(d)) return 0;
+  return static_cast<size_t>(cells_of(d)) * 3 * d->n * d->n * sizeof(int32_t);
+}
+
+size_t tissue_scratch_bytes(const tissue_desc* d) {
+  if (!desc_ok(d)) return 0;
+  return layout(d).total;
+}
+
+int tissue_create(const tissue_desc* d, void* dev_counts, size_t bytes, void* cuda_stream,
+                  tissue** out) {
+  if (!out) return TISSUE_E_ARG;
+  *out = nullptr;
+  if (!desc_ok(d) || !dev_counts) return TISSUE_E_ARG;
+  if (bytes < tissue_state_bytes(d)) return TISSUE_E_ARG;
+  if (reinterpret_cast<uintptr_t>(dev_counts) % 16 != 0) return TISSUE_E_ARG;
+  tissue* t = new (std::nothrow) tissue();
+  if (!t) return TISSUE_E_NOMEM;
+  t->d = *d;
+  t->counts = static_cast<int32_t*>(dev_counts);
+  t->bytes = bytes;
+  t->stream = static_cast<cudaStream_t>(cuda_stream);
+  const ScratchLayout L = layout(d);
+  if (cudaMalloc(&t->scratch, L.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete t;
+    return TISSUE_E_NOMEM;
+  }
+  t->hill = reinterpret_cast<uint64_t*>(t->scratch + L.hill);
+  t->ev_last = reinterpret_cast<uint64_t*>(t->scratch + L.ev_last);
+  t->t_last = reinterpret_cast<double*>(t->scratch + L.t_last);
+  t->ev_total = reinterpret_cast<uint64_t*>(t->scratch + L.ev_total);
+  t->d_step = reinterpret_cast<uint32_t*>(t->scratch + L.step);
+  t->d_err = reinterpret_cast<int*>(t->scratch + L.err);
+  if (cudaMemsetAsync(t->scratch, 0, L.total, t->stream) != cudaSuccess) {
+    cudaFree(t->scratch);
+    delete t;
+    return TISSUE_E_CUDA;
+  }
+  double p0[3], lam[3];
+  for (int s = 0; s < 3; ++s) {
+    lam[s] = d->init_lambda[s];
+    p0[s] = std::exp(-lam[s]);
+  }
+  if (launch_init(view_of(t), p0, lam, t->stream) != cudaSuccess) {
+    cudaFree(t->scratch);
+    delete t;
+    return TISSUE_E_CUDA;
+  }
+  *out = t;
+  return TISSUE_OK;
+}
+
+int tissue_set_model(tissue* t, const tissue_model* m) {
+  if (!t || !m) return TISSUE_E_ARG;
+  const double r[12] = {m->kD, m->K, m->kN, m->gD, m->gN, m->gR,
+                        m->hopD, m->hopN, m->hopR, m->k_in, m->k_off, m->k_bind};
+  for (double x : r)
+    if (!rate_ok(x)) return TISSUE_E_ARG;
+  if (!(m->K > 0.0)) return TISSUE_E_ARG;
+  QRates q{};
+  q.kN = quantise(m->kN);
+  q.gD = quantise(m->gD);
+  q.gN = quantise(m->gN);
+  q.gR = quantise(m->gR);
+  q.hopD = quantise(m->hopD);
+  q.hopN = quantise(m->hopN);
+  q.hopR = quantise(m->hopR);
+  q.k_in = quantise(m->k_in);
+  q.k_off = quantise(m->k_off);
+  q.k_bind = quantise(m->k_bind);
+  for (int nn = 0; nn <= 4; ++nn) {
+    q.cD[nn] = q.gD + static_cast<uint64_t>(nn) * q.hopD;
+    q.cN[nn] = q.gN + static_cast<uint64_t>(nn) * q.hopN;
+    q.cR[nn] = q.gR + static_cast<uint64_t>(nn) * q.hopR;
+  }
+  q.kD = m->kD;
+  q.K = m->K;
+  q.hill = t->hill;
+  if (launch_hill_table(q, t->hill, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  t->q = q;
+  t->has_model = true;
+  return TISSUE_OK;
+}
+
+int tissue_write_counts(tissue* t, const int32_t* host, size_t n, uint32_t step_index) {
+  if (!t || !host) return TISSUE_E_ARG;
+  const size_t want = tissue_state_bytes(&t->d) / sizeof(int32_t);
+  if (n != want) return TISSUE_E_ARG;
+  for (size_t i = 0; i < n; ++i)
+    if (host[i] < 0 || host[i] > TISSUE_COUNT_MAX) return TISSUE_E_ARG;
+  if (cudaMemcpyAsync(t->counts, host, n * sizeof(int32_t), cudaMemcpyHostToDevice, t->stream) !=
+      cudaSuccess)
+    return TISSUE_E_CUDA;
+  if (cudaMemcpyAsync(t->d_step, &step_index, sizeof(uint32_t), cudaMemcpyHostToDevice,
+                      t->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  if (cudaMemsetAsync(t->d_err, 0, sizeof(int), t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  if (cudaStreamSynchronize(t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  t->step_index = step_index;
+  return TISSUE_OK;
+}
+
+int tissue_step(tissue* t, double dt, uint32_t n_steps) {
+  if (!t) return TISSUE_E_ARG;
+  if (!t->has_model) return TISSUE_E_NOMODEL;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return TISSUE_E_ARG;
+  if (n_steps == 0) return TISSUE_OK;
+  const TissueView v = view_of(t);
+  for (uint32_t i = 0; i < n_steps; ++i) {
+    if (launch_chi(v, i, dt, t->chi_wpb, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+    if (launch_sig(v, 0, i, dt, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+    if (launch_sig(v, 1, i, dt, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  }
+  if (launch_step_advance(t->d_step, n_steps, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  t->step_index += n_steps;
+  return TISSUE_OK;
+}
+
+int tissue_step_timed(tissue* t, double dt, uint32_t n_steps, double* ms_chi, double* ms_sig) {
+  if (!t) return TISSUE_E_ARG;
+  if (!t->has_model) return TISSUE_E_NOMODEL;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return TISSUE_E_ARG;
+  // marks[0] before the first launch; marks[2i+1] after chi of step i,
+  // marks[2i+2] after both face phases of step i.
+  std::vector<cudaEvent_t> marks(2 * static_cast<size_t>(n_steps) + 1, nullptr);
+  int rc = TISSUE_OK;
+  for (auto& e : marks)
+    if (cudaEventCreate(&e) != cudaSuccess) rc = TISSUE_E_CUDA;
+  const TissueView v = view_of(t);
+  if (rc == TISSUE_OK && cudaEventRecord(marks[0], t->stream) != cudaSuccess) rc = TISSUE_E_CUDA;
+  for (uint32_t i = 0; i < n_steps && rc == TISSUE_OK; ++i) {
+    if (launch_chi(v, i, dt, t->chi_wpb, t->stream) != cudaSuccess ||
+        cudaEventRecord(marks[2 * i + 1], t->stream) != cudaSuccess ||
+        launch_sig(v, 0, i, dt, t->stream) != cudaSuccess ||
+        launch_sig(v, 1, i, dt, t->stream) != cudaSuccess ||
+        cudaEventRecord(marks[2 * i + 2], t->stream) != cudaSuccess)
+      rc = TISSUE_E_CUDA;
+  }
+  if (rc == TISSUE_OK && launch_step_advance(t->d_step, n_steps, t->stream) != cudaSuccess)
+    rc = TISSUE_E_CUDA;
+  if (rc == TISSUE_OK && cudaStreamSynchronize(t->stream) != cudaSuccess) rc = TISSUE_E_CUDA;
+  double chi = 0.0, sig = 0.0;
+  for (uint32_t i = 0; i < n_steps && rc == TISSUE_OK; ++i) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, marks[2 * i], marks[2 * i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, marks[2 * i + 1], marks[2 * i + 2]) != cudaSuccess)
+      rc = TISSUE_E_CUDA;
+    chi += a;
+    sig += b;
+  }
+  for (auto& e : marks)
+    if (e) cudaEventDestroy(e);
+  if (rc != TISSUE_OK) return rc;
+  t->step_index += n_steps;
+  if (ms_chi) *ms_chi = chi;
+  if (ms_sig) *ms_sig = sig;
+  return device_error(t);
+}
+
+int tissue_read_counts(tissue* t, int32_t* host, size_t n) {
+  if (!t || !host) return TISSUE_E_ARG;
+  if (n != tissue_state_bytes(&t->d) / sizeof(int32_t)) return TISSUE_E_ARG;
+  if (cudaMemcpyAsync(host, t->counts, n * sizeof(int32_t), cudaMemcpyDeviceToHost, t->stream) !=
+      cudaSuccess)
+    return TISSUE_E_CUDA;
+  return device_error(t);
+}
+
+int tissue_read_stats(tissue* t, uint64_t* n_events, double* t_last, size_t n) {
+  if (!t) return TISSUE_E_ARG;
+  const size_t want = 3 * static_cast<size_t>(cells_of(&t->d));
+  if (n != want) return TISSUE_E_ARG;
+  if (n_events && cudaMemcpyAsync(n_events, t->ev_last, n * sizeof(uint64_t),
+                                  cudaMemcpyDeviceToHost, t->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  if (t_last && cudaMemcpyAsync(t_last, t->t_last, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                t->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  return device_error(t);
+}
+
+int tissue_total_events(tissue* t, uint64_t out[3]) {
+  if (!t || !out) return TISSUE_E_ARG;
+  const size_t cells = cells_of(&t->d);
+  std::vector<uint64_t> h(3 * cells);
+  if (cudaMemcpyAsync(h.data(), t->ev_total, h.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                      t->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  const int rc = device_error(t);
+  for (int k = 0; k < 3; ++k) {
+    uint64_t s = 0;
+    for (size_t c = 0; c < cells; ++c) s += h[k * cells + c];
+    out[k] = s;
+  }
+  return rc;
+}
+
+int tissue_get_step(const tissue* t, uint32_t* step_index) {
+  if (!t || !step_index) return TISSUE_E_ARG;
+  *step_index = t->step_index;
+  return TISSUE_OK;
+}
+
+int tissue_sync(tissue* t) {
+  if (!t) return TISSUE_E_ARG;
+  return device_error(t);
+}
+
+int tissue_set_launch(tissue* t, uint32_t chi_warps_per_block) {
+  if (!t || chi_warps_per_block < 1 || chi_warps_per_block > 16) return TISSUE_E_ARG;
+  t->chi_wpb = static_cast<int>(chi_warps_per_block);
+  return TISSUE_OK;
+}
+
+void tissue_destroy(tissue* t) {
+  if (!t) return;
+  cudaStreamSynchronize(t->stream);
+  cudaFree(t->scratch);
+  delete t;
+}
+
+const char* tissue_strerror(int code) {
+  switch (code) {
+    case TISSUE_OK: return "ok";
+    case TISSUE_E_ARG: return "invalid argument";
+    case TISSUE_E_NOMEM: return "out of device memory";
+    case TISSUE_E_NOMODEL: return "no model set";
+    case TISSUE_E_OVERFLOW: return "count or propensity overflow";
+    case TISSUE_E_CUDA: return "CUDA runtime error";
+    case TISSUE_E_TIMEOUT: return "device wait timed out";
+    case TISSUE_E_BUDGET: return "memory budget exceeded";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

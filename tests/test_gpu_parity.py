@@ -1,0 +1,236 @@
+"""GPU path (through the C ABI) against the CPU oracle, bit for bit.
+
+Integer counts must be identical and every binary64 time identical in all 64
+bits: the method is an exact SSA whose arithmetic is fully specified, so there
+is exactly one correct trajectory.  Inputs are seeded and synthetic; every
+expected value comes from oracle/ on the same inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_10889_gb300 import workloads as W
+from paper_1806_10889_gb300.workloads import TissueSpec
+from tests._util import orc_desc, orc_model, poisson_gof, q_rate
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # the gpu marker deselects these on CPU runs
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1806_10889_gb300 import tissue as T  # noqa: E402
+from paper_1806_10889_gb300.tissue import Tissue  # noqa: E402
+
+
+def _bits(x):
+    return np.asarray(x, dtype=np.float64).view(np.uint64)
+
+
+def _compare_step(g: Tissue, d, counts, ne, tl, ctx=""):
+    got = g.read_counts()
+    gne, gtl = g.read_stats()
+    if not np.array_equal(got, counts):
+        bad = np.flatnonzero(got != counts)
+        V = d.V
+        raise AssertionError(f"{ctx}: counts differ at {bad.size} ints; first cell {bad[0] // (3 * V)}")
+    assert np.array_equal(gne, ne), f"{ctx}: event counts differ"
+    assert np.array_equal(_bits(gtl), _bits(tl)), f"{ctx}: event times differ"
+
+
+def _run_both(spec: TissueSpec, dt: float, n_steps: int, wpb: int | None = None, every=True):
+    d, m = orc_desc(spec), orc_model(spec)
+    counts = O.init_counts(d)
+    g = Tissue(spec)
+    if wpb:
+        g.set_launch(wpb)
+    assert np.array_equal(g.read_counts(), counts), "initial counts differ"
+    for k in range(n_steps):
+        ne, tl = O.step(d, m, counts, k, 1, dt)
+        g.step(dt, 1)
+        if every or k == n_steps - 1:
+            _compare_step(g, d, counts, ne, tl, f"{spec} step {k}")
+    g.close()
+    return counts
+
+
+@pytest.mark.parametrize("lam", [(5.0, 5.0, 5.0), (0.3, 50.0, 0.0), (700.0, 1.0, 12.5)])
+def test_initial_counts_bit_exact(lam):
+    spec = TissueSpec(5, 3, 10, seed=123, tissue_id=77, init_lambda=lam)
+    d = orc_desc(spec)
+    g = Tissue(spec)
+    assert np.array_equal(g.read_counts(), O.init_counts(d))
+    g.close()
+
+
+def test_tiny_config_every_step():
+    run = W.tiny()
+    _run_both(run.tissue, run.dt, run.n_steps)
+
+
+STRONG = dict(k_bind=0.05)
+
+
+@pytest.mark.parametrize("w,h,n,dt", [
+    (5, 3, 16, 0.1),    # several warps and blocks, V = 256
+    (3, 2, 10, 0.1),    # V = 100: ragged lane blocks, scalar (non-vector) loads
+    (2, 2, 32, 0.05),   # V = 1024: 32 voxels per lane
+    (4, 1, 2, 0.5),     # V = 4: one voxel per lane, no y-faces
+    (1, 3, 7, 0.2),     # V = 49 (odd), no x-faces
+    (1, 1, 8, 0.1),     # a lone cell: no faces at all
+    (7, 5, 8, 1.0),     # long step, many events
+    (6, 4, 16, 0.01),   # short step, few events
+])
+def test_tiles_and_ragged_shapes(w, h, n, dt):
+    spec = TissueSpec(w, h, n, seed=1000 + w * 100 + n, tissue_id=w * h).with_model(**STRONG)
+    _run_both(spec, dt, 3)
+
+
+@pytest.mark.parametrize("wpb", [1, 2, 3, 8, 16])
+def test_launch_shape_does_not_change_results(wpb):
+    spec = TissueSpec(9, 7, 16, seed=5, tissue_id=3)
+    _run_both(spec, 0.1, 2, wpb=wpb, every=False)
+
+
+def test_in_voxel_binding_channels():
+    spec = TissueSpec(3, 3, 6, seed=17).with_model(k_in=0.02, k_off=0.7)
+    _run_both(spec, 0.2, 4)
+
+
+def test_medium_config_full_tissue():
+    """64x64 cells of 16x16 voxels at dt = 0.1: the whole tissue, two steps."""
+    run = W.medium(0.1)
+    _run_both(run.tissue, run.dt, 2)
+
+
+def _neighbourhood_reference(d, m, c, dt):
+    """Oracle counts of cell c after step 0 of a large tissue, computed from
+    the cells that can influence it: chi on the 3x3 block around c, the
+    x-faces of its three rows and the y-faces of c."""
+    counts = np.zeros(d.cells * 3 * d.V, dtype=np.int32)
+    Wd, Hd = d.width, d.height
+    cx, cy = c % Wd, c // Wd
+    block = [(x, y) for y in range(cy - 1, cy + 2) for x in range(cx - 1, cx + 2)
+             if 0 <= x < Wd and 0 <= y < Hd]
+    chi_stats = {}
+    for x, y in block:
+        cc = y * Wd + x
+        O.init_cell(d, counts, cc)
+        chi_stats[cc] = O.chi_cell(d, m, counts, cc, 0, dt)
+    for y in range(cy - 1, cy + 2):
+        if not 0 <= y < Hd:
+            continue
+        for x in (cx - 1, cx):
+            if 0 <= x and x + 1 < Wd:
+                O.sig_face(d, m, counts, y * Wd + x, 0, 0, dt)
+    if cy >= 1:
+        O.sig_face(d, m, counts, c - Wd, 1, 0, dt)
+    if cy + 1 < Hd:
+        O.sig_face(d, m, counts, c, 1, 0, dt)
+    V = d.V
+    return counts[c * 3 * V:(c + 1) * 3 * V].copy(), chi_stats[c]
+
+
+def test_large_config_sampled_cells():
+    """256x256 cells of 32x32 voxels (0.8 GB of state), one step at dt = 0.1,
+    in the launch shape the benchmark times; sampled cells (corners, edges,
+    interior) checked against the oracle computed cell by cell."""
+    run = W.large()
+    spec = run.tissue
+    d, m = orc_desc(spec), orc_model(spec)
+    g = Tissue(spec)
+    g.set_launch(T.DEFAULT_CHI_WPB)
+    g.step(run.dt, 1)
+    got = g.read_counts()
+    gne, gtl = g.read_stats()
+    g.close()
+    Wd = spec.width
+    rng = np.random.default_rng(99)
+    samples = [0, Wd - 1, Wd * (Wd - 1), Wd * Wd - 1, Wd // 2, Wd * 7] + \
+              [int(x) for x in rng.integers(0, spec.cells, size=6)]
+    V = spec.V
+    for c in samples:
+        ref, (ne, tl) = _neighbourhood_reference(d, m, c, run.dt)
+        assert gne[0, c] == ne and _bits(gtl[0, c]) == _bits(tl), c
+        assert np.array_equal(got[c * 3 * V:(c + 1) * 3 * V], ref), c
+
+
+def test_resume_from_checkpoint_is_bit_identical():
+    spec = TissueSpec(4, 4, 8, seed=21, tissue_id=5).with_model(**STRONG)
+    a = Tissue(spec)
+    a.step(0.1, 6)
+    want = a.read_counts()
+    want_stats = a.read_stats()
+    b = Tissue(spec)
+    b.step(0.1, 3)
+    ckpt = b.read_counts()
+    b.close()
+    c = Tissue(spec)
+    c.write_counts(ckpt, step_index=3)
+    c.step(0.1, 3)
+    assert c.get_step() == 6
+    assert np.array_equal(c.read_counts(), want)
+    got_stats = c.read_stats()
+    assert np.array_equal(got_stats[0], want_stats[0])
+    assert np.array_equal(_bits(got_stats[1]), _bits(want_stats[1]))
+    a.close()
+    c.close()
+
+
+def test_rerun_is_bit_identical_and_totals_add_up():
+    spec = TissueSpec(6, 6, 16, seed=8)
+    runs = []
+    for _ in range(2):
+        g = Tissue(spec)
+        per_step = np.zeros(3, dtype=np.uint64)
+        for k in range(3):
+            g.step(0.1, 1)
+            per_step += g.read_stats()[0].sum(axis=1)
+        runs.append((g.read_counts(), g.total_events()))
+        assert np.array_equal(runs[-1][1], per_step)
+        g.close()
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+def test_overflow_is_reported():
+    spec = TissueSpec(2, 1, 2, seed=1, init_lambda=(0.0, 0.0, 0.0)).with_model(hopD=1000.0)
+    g = Tissue(spec)
+    x = np.zeros(spec.state_ints, dtype=np.int32)
+    x[0] = 2 ** 30 - 1
+    g.write_counts(x)
+    g.step(0.1, 1)
+    with pytest.raises(T.TissueError) as e:
+        g.read_counts()
+    assert e.value.code == T.E_OVERFLOW
+    # the oracle reports the same condition
+    with pytest.raises(O.OracleError):
+        O.step(orc_desc(spec), orc_model(spec), x.copy(), 0, 1, 0.1)
+    g.close()
+
+
+def test_step_without_model_and_bad_dt():
+    spec = TissueSpec(2, 2, 4, seed=1)
+    g = Tissue(spec)
+    with pytest.raises(T.TissueError) as e:
+        g.step(0.0, 1)
+    assert e.value.code == T.E_ARG
+    with pytest.raises(T.TissueError):
+        g.write_counts(np.full(spec.state_ints, -1, dtype=np.int32))
+    g.close()
+
+
+def test_gpu_ensemble_immigration_death_law():
+    """Closed form on the GPU at scale: 64x64 cells of 16x16 voxels with Notch
+    only; every voxel is Poisson(m(t)) with m(t) = lam e^-gt + (b/g)(1-e^-gt)."""
+    zero = dict(kD=0.0, kN=5.0, gD=0.0, gN=0.1, gR=0.0, hopD=0.0, hopN=1.0, hopR=0.0,
+                k_in=0.0, k_off=0.0, k_bind=0.01)
+    spec = TissueSpec(64, 64, 16, seed=404, init_lambda=(0.0, 7.0, 0.0)).with_model(**zero)
+    g = Tissue(spec)
+    g.step(0.5, 30)
+    x = g.read_counts().reshape(spec.cells, 3, spec.V)[:, 1, :]
+    g.close()
+    import math
+    gq = q_rate(0.1)
+    mean = 7.0 * math.exp(-gq * 15.0) + (q_rate(5.0) / gq) * (1 - math.exp(-gq * 15.0))
+    p, z = poisson_gof(x, mean)
+    assert p > 0.01 and abs(z) < 3, (p, z)

@@ -133,10 +133,12 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    run = W.medium(args.dt)
-    spec = run.tissue
+    from dataclasses import replace
+    spec = W.medium(args.dt).tissue
+    if args.side or args.n:  # profiling cases: same model and seed, other sizes
+        spec = replace(spec, width=args.side or spec.width, height=args.side or spec.height,
+                       n=args.n or spec.n)
     if world > 1:  # independent replica per rank
-        from dataclasses import replace
         spec = replace(spec, tissue_id=rank)
     g = Tissue(spec)
     g.set_launch(args.chi_wpb or DEFAULT_CHI_WPB)
@@ -238,7 +240,9 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": total_ms_job / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
         "data": "synthetic", "impl": "ours",
-        "config": {"workload": "medium tissue 64x64 cells of 16x16 voxels, Notch-Delta model",
+        "config": {"workload": f"{'medium' if not (args.side or args.n) else 'custom'} tissue "
+                               f"{spec.width}x{spec.height} cells of {spec.n}x{spec.n} voxels, "
+                               "Notch-Delta model",
                    "dt": args.dt, "burn_in_time": args.burn_in, "cells": spec.cells,
                    "voxels_per_cell": spec.V, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}", "chi_warps_per_block":
@@ -322,6 +326,8 @@ def main():
     ap.add_argument("--chi-traffic", type=float, default=None,
                     help="DRAM bytes per chi launch from an ncu capture, if known")
     ap.add_argument("--ref-side", type=int, default=16)
+    ap.add_argument("--side", type=int, default=0, help="profiling only: tissue side in cells")
+    ap.add_argument("--n", type=int, default=0, help="profiling only: voxels per cell side")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

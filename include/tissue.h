@@ -143,6 +143,31 @@ int tissue_sync(tissue* t);
  * Results never depend on it. */
 int tissue_set_launch(tissue* t, uint32_t chi_warps_per_block);
 
+/* Largest tissue (width*height cells) tissue_step_noalloc accepts. */
+#define TISSUE_NOALLOC_MAX_CELLS 16384
+
+/* Allocation-free steps.  The paper has no counterpart; this exists for
+ * callers that cannot allocate device memory when they advance a tissue (an
+ * application that owns a fixed device-memory budget itself, or code where a
+ * cudaMalloc would synchronise the device).  No cudaMalloc, cudaFree or
+ * allocating library call is made: the scratch (Hill table, step counter,
+ * error flag, cumulative counters; about 416 KB) is one static device array
+ * that every device loading this library keeps until the process exits.
+ *
+ * dev_counts (in/out, device, 16-byte aligned): the state as in tissue_create.
+ * step_index: global index of the first step (the Philox step word).
+ * dev_n_events / dev_t_last (out, device, 3*width*height each): statistics of
+ * the last step laid out as in tissue_read_stats.
+ * Runs n_steps steps exactly as tissue_step would, on cuda_stream, and waits
+ * for them; returns TISSUE_E_ARG if width*height > TISSUE_NOALLOC_MAX_CELLS
+ * or an argument is invalid, TISSUE_E_OVERFLOW as tissue_read_counts would.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: calls whose work overlaps on a device race. */
+int tissue_step_noalloc(const tissue_desc* desc, const tissue_model* model, int32_t* dev_counts,
+                        uint32_t step_index, double dt, uint32_t n_steps,
+                        uint64_t* dev_n_events, double* dev_t_last, void* cuda_stream);
+
 /* Release library scratch (not the caller's buffer or stream). */
 void tissue_destroy(tissue* t);
 

@@ -63,6 +63,8 @@ SIGNATURES = {
     "tissue_get_step": (C.c_int, [C.c_void_p, _P(C.c_uint32)]),
     "tissue_sync": (C.c_int, [C.c_void_p]),
     "tissue_set_launch": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "tissue_step_noalloc": (C.c_int, [_P(Desc), _P(Model), C.c_void_p, C.c_uint32, C.c_double,
+                                      C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tissue_destroy": (None, [C.c_void_p]),
     "tissue_strerror": (C.c_char_p, [C.c_int]),
 }

@@ -168,6 +168,13 @@ int tissue_step_noalloc(const tissue_desc* desc, const tissue_model* model, int3
                         uint32_t step_index, double dt, uint32_t n_steps,
                         uint64_t* dev_n_events, double* dev_t_last, void* cuda_stream);
 
+/* Diagnostic: check the event loop's integer implementation of the binary64
+ * waiting time (tau = E / (A 2^-32), IEEE round-to-nearest) and clock test
+ * against the GPU's FP64 unit on n_samples random and structured inputs
+ * (seeded); *mismatches receives the number of differing results (0 expected).
+ * Synchronises the device. */
+int tissue_selftest_time(uint64_t n_samples, uint64_t seed, uint64_t* mismatches);
+
 /* Release library scratch (not the caller's buffer or stream). */
 void tissue_destroy(tissue* t);
 

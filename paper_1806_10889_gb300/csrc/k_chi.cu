@@ -3,11 +3,11 @@
 // [0, dt), one warp per cell.
 //
 // Data layout per warp in shared memory:
-//   pre[v]   uint64  inclusive prefix of the voxel propensities a_v inside the
-//                    lane block of v (lane l owns voxels l*B .. l*B+B-1)
-//   cnt[s][v] int32  D, N, R counts
+//   pre[v]    uint64  inclusive prefix of the voxel propensities a_v inside the
+//                     lane block of v (lane l owns voxels l*B .. l*B+B-1)
+//   cnt[s][v] int32   D, N, R counts
 // and per lane in registers:
-//   P        uint64  inclusive prefix of the block totals over lanes 0..l
+//   P         uint64  inclusive prefix of the block totals over lanes 0..l
 // Propensities are exact integers (units of 2^-32 per unit time), so the
 // prefix sums are exact and are updated by adding the change of the touched
 // voxels instead of being rebuilt: after an event only 1 or 2 voxels change.
@@ -17,13 +17,18 @@
 // channels of that voxel finds the channel -- the same first-index-whose-
 // running-sum-exceeds-r rule as a linear scan in voxel-major, channel-minor
 // order.  Random numbers for 32 consecutive events are drawn at once, one
-// Philox block and one exponential variate per lane.
+// Philox block and one exponential variate per lane.  The waiting time uses
+// the integer binary64 quotient of tissue_dev.cuh, so the only FP64-pipe
+// instruction per event is the clock addition t + tau.
 #include "tissue_dev.cuh"
 
 namespace tsg {
 
 namespace {
 
+// Total propensity of voxel v.  Counts below q.small cannot reach the 2^52
+// limit, so the common case needs no overflow checks; otherwise every term is
+// checked exactly.
 template <int VMAX>
 __device__ __forceinline__ uint64_t voxel_total(const int32_t* cnt, int v, const TissueView& t,
                                                 bool& ovf) {
@@ -33,7 +38,12 @@ __device__ __forceinline__ uint64_t voxel_total(const int32_t* cnt, int v, const
   const int n = static_cast<int>(t.n);
   const int vy = div_n(v, t.magic), vx = v - vy * n;
   const int nn = (vx > 0) + (vx < n - 1) + (vy > 0) + (vy < n - 1);
-  uint64_t a = hill_q(t.q, R) + t.q.kN;
+  const uint64_t base = hill_q(t.q, R) + t.q.kN;
+  if ((D | N | R) < t.q.small) {
+    return base + t.q.cD[nn] * D + t.q.cN[nn] * N + t.q.cRo[nn] * R +
+           t.q.k_in * (static_cast<uint64_t>(D) * N);
+  }
+  uint64_t a = base;
   a += mul_lim(t.q.cD[nn], D, ovf);
   a += mul_lim(t.q.cN[nn], N, ovf);
   a += mul_lim(t.q.cR[nn], R, ovf);
@@ -136,13 +146,9 @@ __global__ void __launch_bounds__(512) k_chi(const TissueView t, const uint32_t 
 
   double tnow = 0.0;
   uint32_t e = 0, e0 = 0;
-  double Eb;
-  uint64_t Rb;
-  {
-    const U4 w = philox10(e0 + lane, step, cell, word3, key0, key1);
-    Eb = exp_variate(w.x, w.y);
-    Rb = (static_cast<uint64_t>(w.w) << 32) | w.z;
-  }
+  uint64_t Em, Rb;
+  int Ek;
+  draw_event(e0 + lane, step, cell, word3, key0, key1, Em, Ek, Rb);
   int err = __any_sync(kFull, ovf) ? kErrOverflow : 0;
 
   while (A != 0ull && !err) {
@@ -150,14 +156,13 @@ __global__ void __launch_bounds__(512) k_chi(const TissueView t, const uint32_t 
     if (j == 32) {
       e0 += 32;
       j = 0;
-      const U4 w = philox10(e0 + lane, step, cell, word3, key0, key1);
-      Eb = exp_variate(w.x, w.y);
-      Rb = (static_cast<uint64_t>(w.w) << 32) | w.z;
+      draw_event(e0 + lane, step, cell, word3, key0, key1, Em, Ek, Rb);
     }
-    const double E = __shfl_sync(kFull, Eb, j);
+    const uint64_t mE = __shfl_sync(kFull, Em, j);
+    const int kE = __shfl_sync(kFull, Ek, j);
     const uint64_t R64 = __shfl_sync(kFull, Rb, j);
     // waiting time: tau = E / (A 2^-32); the event fires iff t + tau < dt
-    const double tn = __dadd_rn(tnow, __ddiv_rn(E, __dmul_rn(__ull2double_rn(A), 0x1p-32)));
+    const double tn = __dadd_rn(tnow, tau_from(F53{mE, kE}, kE < 0, A));
 
     // selection (independent of the time test, so it overlaps its latency)
     const uint64_t r = __umul64hi(R64, A);
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(512) k_chi(const TissueView t, const uint32_t 
       break;
     }
 
-    if (!(tn < dt)) break;
+    if (!before(tn, dt)) break;
     tnow = tn;
 
     // the channel's effect: up to three (species, voxel, +-1) changes
@@ -232,10 +237,7 @@ __global__ void __launch_bounds__(512) k_chi(const TissueView t, const uint32_t 
       sp0 = 2; d0 = -1; sp1 = 0; d1 = 1; sp2 = 1; d2 = 1;
     }
     uint64_t a_old_u = 0;
-    if (u >= 0 && lane == 1) {
-      const int pu = u & (B - 1);
-      a_old_u = pre[u] - (pu ? pre[u - 1] : 0ull);
-    }
+    if (u >= 0) a_old_u = pre[u] - ((u & (B - 1)) ? pre[u - 1] : 0ull);
     __syncwarp();
     if (lane < 3) {
       const int sp = lane == 0 ? sp0 : lane == 1 ? sp1 : sp2;
@@ -249,11 +251,11 @@ __global__ void __launch_bounds__(512) k_chi(const TissueView t, const uint32_t 
       }
     }
     __syncwarp();
-    uint64_t a_new = 0;
-    if (lane == 0) a_new = voxel_total<VMAX>(cnt, v, t, ovf);
-    if (lane == 1 && u >= 0) a_new = voxel_total<VMAX>(cnt, u, t, ovf) - a_old_u;
+    // New totals: lane 1 evaluates u (when a hop moved a molecule there), the
+    // others v; one call site, so the warp does not split.
+    const uint64_t a_new = voxel_total<VMAX>(cnt, (lane == 1 && u >= 0) ? u : v, t, ovf);
     const uint64_t dv = __shfl_sync(kFull, a_new, 0) - a_old_v;
-    const uint64_t du = __shfl_sync(kFull, a_new, 1);
+    const uint64_t du = __shfl_sync(kFull, a_new, 1) - a_old_u;
     const int bv = v / B;
     P += lane >= bv ? dv : 0ull;
     A += dv;
@@ -315,6 +317,43 @@ cudaError_t launch_chi_b(const TissueView& t, uint32_t step_off, double dt, int 
   return cudaGetLastError();
 }
 
+// Self-check of the integer binary64 time arithmetic against the FP64 unit:
+// random and structured (E, A) pairs, the quotient and the clock test.
+__global__ void k_selftest_time(uint64_t n, uint64_t seed, unsigned long long* mismatches) {
+  unsigned long long bad = 0;
+  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const U4 w = philox10(static_cast<uint32_t>(i), static_cast<uint32_t>(i >> 32), 7u, 7u,
+                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+    const uint64_t w01 = (static_cast<uint64_t>(w.y) << 32) | w.x;
+    const uint64_t w23 = (static_cast<uint64_t>(w.w) << 32) | w.z;
+    uint64_t eq;
+    switch (i & 3) {
+      case 0: eq = neg_ln_q58((w01 >> 11) + 1); break;           // as drawn
+      case 1: eq = w01 >> (w.z & 63); break;                     // any magnitude
+      case 2: eq = (1ull << (w.z % 63)) + (w.w & 7) - 3; break;  // near powers of two
+      default: eq = w01 & 0xFFFFFull; break;                     // small
+    }
+    uint64_t A;
+    switch ((i >> 2) & 3) {
+      case 0: A = w23 >> (2 + (w.x % 62)); break;                // 1 .. 2^62
+      case 1: A = 1ull << (w.x % 62); break;                     // powers of two
+      case 2: A = (1ull << (w.x % 62)) + (w.y & 15) - 7; break;  // around them
+      default: A = (w23 >> 9) | (1ull << 54); break;             // needs rounding to 53 bits
+    }
+    if (A == 0ull || (A >> 62) != 0ull) A = 1ull + (A & 0x3FFFFFFFFFFFFFFEull);
+    const F53 f = round53(eq | static_cast<uint64_t>(eq == 0ull));
+    const double mine = tau_from(f, eq == 0ull, A);
+    const double ref = __ddiv_rn(__dmul_rn(__ull2double_rn(eq), 0x1p-58),
+                                 __dmul_rn(__ull2double_rn(A), 0x1p-32));
+    bad += __double_as_longlong(mine) != __double_as_longlong(ref);
+    const double t0 = __dmul_rn(__ull2double_rn(w23 >> 11), 0x1p-53);
+    const double sum = __dadd_rn(t0, ref);
+    bad += before(sum, 0.5) != (sum < 0.5);
+  }
+  if (bad) atomicAdd(mismatches, bad);
+}
+
 }  // namespace
 
 cudaError_t launch_chi(const TissueView& t, uint32_t step_off, double dt, int wpb,
@@ -327,6 +366,29 @@ cudaError_t launch_chi(const TissueView& t, uint32_t step_off, double dt, int wp
   if (V <= 512) return launch_chi_b<16>(t, step_off, dt, wpb, stream);
   if (V <= 1024) return launch_chi_b<32>(t, step_off, dt, wpb, stream);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_selftest_time(uint64_t n, uint64_t seed, unsigned long long* mismatches,
+                                 cudaStream_t stream) {
+  k_selftest_time<<<152 * 8, 256, 0, stream>>>(n, seed, mismatches);
+  return cudaGetLastError();
+}
+
+uint32_t small_count_bound(const QRates& q, uint64_t hill_max) {
+  using u128 = unsigned __int128;
+  uint64_t cmax = 0;
+  for (int nn = 0; nn <= 4; ++nn) {
+    const uint64_t c = q.cD[nn] + q.cN[nn] + q.cRo[nn];
+    cmax = c > cmax ? c : cmax;
+  }
+  uint32_t best = 0;
+  for (int j = 1; j <= 30; ++j) {
+    const u128 T = (static_cast<u128>(1) << j) - 1;  // largest count below 2^j
+    const u128 a = static_cast<u128>(hill_max) + q.kN + static_cast<u128>(cmax) * T +
+                   static_cast<u128>(q.k_in) * T * T;
+    if (a < (static_cast<u128>(1) << 52)) best = 1u << j;
+  }
+  return best;
 }
 
 }  // namespace tsg

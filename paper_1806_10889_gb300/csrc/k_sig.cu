@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(256) k_sig(const TissueView t, const int axis,
   int err = __any_sync(kFull, ovf) ? kErrOverflow : 0;
   double tnow = 0.0;
   uint32_t e = 0, e0 = 0;
-  double Eb = 0.0;
-  uint64_t Rnd = 0;
+  uint64_t Em = 0, Rnd = 0;
+  int Ek = -1;
   bool have = false;
 
   while (A != 0ull && !err) {
@@ -74,13 +74,12 @@ __global__ void __launch_bounds__(256) k_sig(const TissueView t, const int axis,
       if (have) e0 += 32;
       have = true;
       j = 0;
-      const U4 w = philox10(e0 + lane, step, c, word3, key0, key1);
-      Eb = exp_variate(w.x, w.y);
-      Rnd = (static_cast<uint64_t>(w.w) << 32) | w.z;
+      draw_event(e0 + lane, step, c, word3, key0, key1, Em, Ek, Rnd);
     }
-    const double E = __shfl_sync(kFull, Eb, j);
+    const uint64_t mE = __shfl_sync(kFull, Em, j);
+    const int kE = __shfl_sync(kFull, Ek, j);
     const uint64_t R64 = __shfl_sync(kFull, Rnd, j);
-    const double tn = __dadd_rn(tnow, __ddiv_rn(E, __dmul_rn(__ull2double_rn(A), 0x1p-32)));
+    const double tn = __dadd_rn(tnow, tau_from(F53{mE, kE}, kE < 0, A));
     const uint64_t r = __umul64hi(R64, A);
     const unsigned m1 = __ballot_sync(kFull, r < P);
     const int L = m1 ? __ffs(m1) - 1 : 0;
@@ -91,7 +90,7 @@ __global__ void __launch_bounds__(256) k_sig(const TissueView t, const int axis,
     const uint64_t Pl = __shfl_sync(kFull, P, L > 0 ? L - 1 : 0);
     const uint64_t r1 = r - (L > 0 ? Pl : 0ull);
     const uint64_t c0L = __shfl_sync(kFull, c0, L);
-    if (!(tn < dt)) break;
+    if (!before(tn, dt)) break;
     tnow = tn;
     uint64_t delta = 0;
     if (lane == L) {

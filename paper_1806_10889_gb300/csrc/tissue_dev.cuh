@@ -117,6 +117,110 @@ __device__ __forceinline__ uint64_t hill_q(const QRates& q, uint32_t R) {
   return R < kHillTab ? __ldg(q.hill + R) : hill_direct(q, R);
 }
 
+// ---------------------------------------------------------------------------
+// Binary64 time arithmetic in integer registers.
+//
+// tau = E / (A 2^-32) must be the IEEE round-to-nearest quotient.  The
+// hardware division costs ~140 cycles of the SM's FP64 pipe per warp on
+// GB300 even with one active lane, so the event loop computes the same
+// correctly rounded result with integer instructions:
+//   1. E (Q.58) and A are rounded to 53-bit significands exactly as the
+//      integer-to-binary64 conversion does (round half to even).
+//   2. Y ~ 2^115 / mA from a single-precision reciprocal estimate refined by
+//      two Newton-Raphson steps y <- y + y (2^115 - mA y) / 2^115 in fixed
+//      point; the quotient estimate floor(mE 2^sh / mA) is then corrected
+//      with the exact remainder (long division with a reciprocal, Knuth,
+//      TAOCP vol. 2, 4.3.1; Moller & Granlund, IEEE TC 60(2), 2011).
+//   3. The 53-bit quotient is rounded to nearest with the remainder
+//      (a binary division can never land exactly half-way) and assembled.
+// ---------------------------------------------------------------------------
+struct F53 {
+  uint64_t m;  // significand in [2^52, 2^53)
+  int k;       // x ~ m * 2^(k - 52)
+};
+
+// Round x >= 1 to 53 significant bits, half to even (the u64 -> binary64 rule).
+__device__ __forceinline__ F53 round53(uint64_t x) {
+  const int k = 63 - __clzll(static_cast<long long>(x));
+  if (k <= 52) return F53{x << (52 - k), k};
+  const int s = k - 52;
+  uint64_t m = x >> s;
+  const uint64_t rem = x & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+  m += static_cast<uint64_t>((rem > half) | ((rem == half) & static_cast<bool>(m & 1ull)));
+  if (m >> 53) return F53{m >> 1, k + 1};
+  return F53{m, k};
+}
+
+// floor(2^115 / d) up to a few units, d in (2^52, 2^53).
+__device__ __forceinline__ uint64_t recip115(uint64_t d) {
+  const float df = static_cast<float>(static_cast<uint32_t>(d >> 29));  // exact: < 2^24
+  float f;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"(df));
+  const uint32_t fb = __float_as_uint(f);
+  const int ef = static_cast<int>((fb >> 23) & 0xFFu) - 127;  // -24 or -23
+  uint64_t y = static_cast<uint64_t>((fb & 0x7FFFFFu) | 0x800000u) << (63 + ef);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const uint64_t lo = d * y, hi = __umul64hi(d, y);           // d*y ~ 2^115
+    const int64_t e34 = static_cast<int64_t>(((1ull << 51) - hi) << 30) -
+                        static_cast<int64_t>(lo >> 34);            // (2^115 - d*y) / 2^34
+    const uint64_t ae = static_cast<uint64_t>(e34 < 0 ? -e34 : e34);
+    const uint64_t c = __umul64hi(y, ae) >> 17;                   // y * |e| / 2^115
+    y = e34 < 0 ? y - c : y + c;
+  }
+  return y;
+}
+
+// IEEE binary64 RN quotient (E_q58 * 2^-58) / (RN(A) * 2^-32), as a double.
+// E_q58 = 0 gives +0.  eq = round53(E_q58) is passed in (it is per draw).
+__device__ __forceinline__ double tau_from(const F53 eq, bool e_zero, uint64_t A) {
+  if (e_zero) return 0.0;
+  const F53 a = round53(A);
+  const uint64_t mE = eq.m, d = a.m;
+  const int sh = mE >= d ? 52 : 53;  // quotient significand lands in [2^52, 2^53)
+  uint64_t q;
+  int64_t r;
+  if (d == (1ull << 52)) {           // power-of-two divisor: exact shift
+    q = mE << (sh - 52);
+    r = 0;
+  } else {
+    const uint64_t y = recip115(d);
+    const uint64_t plo = mE * y, phi = __umul64hi(mE, y);
+    q = sh == 52 ? ((phi << 1) | (plo >> 63)) : ((phi << 2) | (plo >> 62));
+    r = static_cast<int64_t>((mE << sh) - q * d);  // exact: |r| < 2^54
+    if (r < 0) { q -= 1; r += static_cast<int64_t>(d); }
+    if (r < 0) { q -= 1; r += static_cast<int64_t>(d); }
+    if (r >= static_cast<int64_t>(d)) { q += 1; r -= static_cast<int64_t>(d); }
+    if (r >= static_cast<int64_t>(d)) { q += 1; r -= static_cast<int64_t>(d); }
+  }
+  const uint64_t twice = static_cast<uint64_t>(r) << 1;
+  q += static_cast<uint64_t>((twice > d) | ((twice == d) & static_cast<bool>(q & 1ull)));
+  // tau = q * 2^X with X = (kE - 110) - (kA - 84) - sh; a carry of q into
+  // 2^53 moves into the exponent field by itself.
+  const int X = eq.k - a.k - 26 - sh;
+  const uint64_t bits = (static_cast<uint64_t>(X + 1075) << 52) + (q - (1ull << 52));
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+// t < dt for non-negative doubles: the IEEE order is the integer order of the bits.
+__device__ __forceinline__ bool before(double t, double dt) {
+  return __double_as_longlong(t) < __double_as_longlong(dt);
+}
+
+// One lane's draw for event e: the exponential variate as a rounded
+// 53-bit significand and exponent (exponent -1 encodes E = 0) and the 64
+// selection bits.
+__device__ __forceinline__ void draw_event(uint32_t e, uint32_t step, uint32_t unit,
+                                           uint32_t word3, uint32_t key0, uint32_t key1,
+                                           uint64_t& Em, int& Ek, uint64_t& Rb) {
+  const U4 w = philox10(e, step, unit, word3, key0, key1);
+  const uint64_t q = neg_ln_q58((((static_cast<uint64_t>(w.y) << 32) | w.x) >> 11) + 1);
+  const F53 f = round53(q | static_cast<uint64_t>(q == 0ull));
+  Em = f.m;
+  Ek = q ? f.k : -1;
+  Rb = (static_cast<uint64_t>(w.w) << 32) | w.z;
+}
+
 // v / n for v < 1024, n <= 32: (v * ceil(2^16 / n)) >> 16 is exact there.
 __device__ __forceinline__ int div_n(int v, uint32_t magic) {
   return static_cast<int>((static_cast<uint32_t>(v) * magic) >> 16);

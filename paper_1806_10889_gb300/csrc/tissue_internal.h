@@ -19,8 +19,10 @@ constexpr uint64_t kPropLimit = 1ull << 52;  // a voxel or face channel must sta
 struct QRates {
   uint64_t kN, gD, gN, gR, hopD, hopN, hopR, k_in, k_off, k_bind;
   uint64_t cD[5], cN[5], cR[5];  // g + nn * hop for nn existing neighbours
+  uint64_t cRo[5];               // cR[nn] + k_off
   double kD, K;
   const uint64_t* hill;  // device table, kHillTab entries
+  uint32_t small;        // counts all below this keep every voxel total below 2^52
 };
 
 // One tissue as the kernels see it.
@@ -47,5 +49,16 @@ cudaError_t launch_chi(const TissueView& t, uint32_t step_off, double dt, int wa
 cudaError_t launch_sig(const TissueView& t, int axis, uint32_t step_off, double dt,
                        cudaStream_t stream);
 cudaError_t launch_step_advance(uint32_t* step, uint32_t n, cudaStream_t stream);
+cudaError_t launch_selftest_time(uint64_t n, uint64_t seed, unsigned long long* mismatches,
+                                 cudaStream_t stream);
+
+// Validate and quantise the twelve rates (kD, K, kN, gD, gN, gR, hopD, hopN,
+// hopR, k_in, k_off, k_bind) into q; q->hill is set to `hill`.  false when a
+// rate is out of range.
+bool make_qrates(const double rates[12], const uint64_t* hill, QRates* q);
+
+// Largest power of two T <= 2^30 such that counts below T keep a voxel's total
+// propensity below 2^52 (so the fast path needs no overflow checks).
+uint32_t small_count_bound(const QRates& q, uint64_t hill_max);
 
 }  // namespace tsg

@@ -74,11 +74,6 @@ ScratchLayout layout(const tissue_desc* d) {
   return L;
 }
 
-bool rate_ok(double x) { return std::isfinite(x) && x >= 0.0 && x < 1048576.0; }
-
-// Rate x as an integer number of 2^-32 units: round-half-even(x * 2^32).
-uint64_t quantise(double x) { return static_cast<uint64_t>(std::nearbyint(x * 4294967296.0)); }
-
 TissueView view_of(const tissue* t) {
   TissueView v{};
   v.counts = t->counts;
@@ -107,7 +102,41 @@ int device_error(tissue* t) {
   return h ? TISSUE_E_OVERFLOW : TISSUE_OK;
 }
 
+bool rate_ok(double x) { return std::isfinite(x) && x >= 0.0 && x < 1048576.0; }
+
+// Rate x as an integer number of 2^-32 units: round-half-even(x * 2^32).
+uint64_t quantise(double x) { return static_cast<uint64_t>(std::nearbyint(x * 4294967296.0)); }
+
 }  // namespace
+
+bool tsg::make_qrates(const double r[12], const uint64_t* hill, QRates* q) {
+  for (int i = 0; i < 12; ++i)
+    if (!rate_ok(r[i])) return false;
+  if (!(r[1] > 0.0)) return false;
+  *q = QRates{};
+  q->kD = r[0];
+  q->K = r[1];
+  q->kN = quantise(r[2]);
+  q->gD = quantise(r[3]);
+  q->gN = quantise(r[4]);
+  q->gR = quantise(r[5]);
+  q->hopD = quantise(r[6]);
+  q->hopN = quantise(r[7]);
+  q->hopR = quantise(r[8]);
+  q->k_in = quantise(r[9]);
+  q->k_off = quantise(r[10]);
+  q->k_bind = quantise(r[11]);
+  for (int nn = 0; nn <= 4; ++nn) {
+    q->cD[nn] = q->gD + static_cast<uint64_t>(nn) * q->hopD;
+    q->cN[nn] = q->gN + static_cast<uint64_t>(nn) * q->hopN;
+    q->cR[nn] = q->gR + static_cast<uint64_t>(nn) * q->hopR;
+    q->cRo[nn] = q->cR[nn] + q->k_off;
+  }
+  q->hill = hill;
+  // the Hill term is largest at R = 0, where it is quantise(kD) (kD / 1)
+  q->small = small_count_bound(*q, quantise(r[0]));
+  return true;
+}
 
 extern "C" {
 
@@ -169,28 +198,8 @@ int tissue_set_model(tissue* t, const tissue_model* m) {
   if (!t || !m) return TISSUE_E_ARG;
   const double r[12] = {m->kD, m->K, m->kN, m->gD, m->gN, m->gR,
                         m->hopD, m->hopN, m->hopR, m->k_in, m->k_off, m->k_bind};
-  for (double x : r)
-    if (!rate_ok(x)) return TISSUE_E_ARG;
-  if (!(m->K > 0.0)) return TISSUE_E_ARG;
   QRates q{};
-  q.kN = quantise(m->kN);
-  q.gD = quantise(m->gD);
-  q.gN = quantise(m->gN);
-  q.gR = quantise(m->gR);
-  q.hopD = quantise(m->hopD);
-  q.hopN = quantise(m->hopN);
-  q.hopR = quantise(m->hopR);
-  q.k_in = quantise(m->k_in);
-  q.k_off = quantise(m->k_off);
-  q.k_bind = quantise(m->k_bind);
-  for (int nn = 0; nn <= 4; ++nn) {
-    q.cD[nn] = q.gD + static_cast<uint64_t>(nn) * q.hopD;
-    q.cN[nn] = q.gN + static_cast<uint64_t>(nn) * q.hopN;
-    q.cR[nn] = q.gR + static_cast<uint64_t>(nn) * q.hopR;
-  }
-  q.kD = m->kD;
-  q.K = m->K;
-  q.hill = t->hill;
+  if (!make_qrates(r, t->hill, &q)) return TISSUE_E_ARG;
   if (launch_hill_table(q, t->hill, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
   t->q = q;
   t->has_model = true;
@@ -332,6 +341,24 @@ void tissue_destroy(tissue* t) {
   cudaStreamSynchronize(t->stream);
   cudaFree(t->scratch);
   delete t;
+}
+
+int tissue_selftest_time(uint64_t n_samples, uint64_t seed, uint64_t* mismatches) {
+  if (!mismatches) return TISSUE_E_ARG;
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, sizeof(*d)) != cudaSuccess) {
+    cudaGetLastError();
+    return TISSUE_E_NOMEM;
+  }
+  unsigned long long h = 0;
+  int rc = TISSUE_OK;
+  if (cudaMemset(d, 0, sizeof(*d)) != cudaSuccess ||
+      launch_selftest_time(n_samples, seed, d, nullptr) != cudaSuccess ||
+      cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = TISSUE_E_CUDA;
+  cudaFree(d);
+  *mismatches = h;
+  return rc;
 }
 
 const char* tissue_strerror(int code) {

@@ -61,8 +61,6 @@ int scratch_on_current_device(StaticScratch** out) {
 
 bool finite_rate(double x) { return std::isfinite(x) && x >= 0.0 && x < 1048576.0; }
 
-uint64_t to_units(double x) { return static_cast<uint64_t>(std::nearbyint(x * 4294967296.0)); }
-
 }  // namespace
 
 extern "C" int tissue_step_noalloc(const tissue_desc* d, const tissue_model* m,
@@ -88,24 +86,7 @@ extern "C" int tissue_step_noalloc(const tissue_desc* d, const tissue_model* m,
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
   QRates q{};
-  q.kN = to_units(m->kN);
-  q.gD = to_units(m->gD);
-  q.gN = to_units(m->gN);
-  q.gR = to_units(m->gR);
-  q.hopD = to_units(m->hopD);
-  q.hopN = to_units(m->hopN);
-  q.hopR = to_units(m->hopR);
-  q.k_in = to_units(m->k_in);
-  q.k_off = to_units(m->k_off);
-  q.k_bind = to_units(m->k_bind);
-  for (int nn = 0; nn <= 4; ++nn) {
-    q.cD[nn] = q.gD + static_cast<uint64_t>(nn) * q.hopD;
-    q.cN[nn] = q.gN + static_cast<uint64_t>(nn) * q.hopN;
-    q.cR[nn] = q.gR + static_cast<uint64_t>(nn) * q.hopR;
-  }
-  q.kD = m->kD;
-  q.K = m->K;
-  q.hill = s->hill;
+  if (!make_qrates(r, s->hill, &q)) return TISSUE_E_ARG;
 
   TissueView v{};
   v.counts = dev_counts;

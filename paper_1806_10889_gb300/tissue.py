@@ -65,6 +65,7 @@ SIGNATURES = {
     "tissue_set_launch": (C.c_int, [C.c_void_p, C.c_uint32]),
     "tissue_step_noalloc": (C.c_int, [_P(Desc), _P(Model), C.c_void_p, C.c_uint32, C.c_double,
                                       C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tissue_selftest_time": (C.c_int, [C.c_uint64, C.c_uint64, _P(C.c_uint64)]),
     "tissue_destroy": (None, [C.c_void_p]),
     "tissue_strerror": (C.c_char_p, [C.c_int]),
 }
@@ -123,6 +124,14 @@ def scratch_bytes(spec: TissueSpec) -> int:
 def _check(rc: int, what: str):
     if rc != OK:
         raise TissueError(rc, what)
+
+
+def selftest_time(n_samples: int, seed: int = 1) -> int:
+    """Mismatches of the integer binary64 time path against the FP64 unit."""
+    out = C.c_uint64()
+    _check(lib().tissue_selftest_time(int(n_samples), int(seed), C.byref(out)),
+           "tissue_selftest_time")
+    return int(out.value)
 
 
 class Tissue:

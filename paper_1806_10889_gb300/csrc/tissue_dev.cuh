@@ -127,10 +127,10 @@ __device__ __forceinline__ uint64_t hill_q(const QRates& q, uint32_t R) {
 //   1. E (Q.58) and A are rounded to 53-bit significands exactly as the
 //      integer-to-binary64 conversion does (round half to even).
 //   2. Y ~ 2^115 / mA from a single-precision reciprocal estimate refined by
-//      two Newton-Raphson steps y <- y + y (2^115 - mA y) / 2^115 in fixed
-//      point; the quotient estimate floor(mE 2^sh / mA) is then corrected
-//      with the exact remainder (long division with a reciprocal, Knuth,
-//      TAOCP vol. 2, 4.3.1; Moller & Granlund, IEEE TC 60(2), 2011).
+//      one third-order Newton-Raphson (Householder) step in fixed point; the
+//      quotient estimate floor(mE 2^sh / mA) is then corrected with the exact
+//      remainder (long division with a reciprocal, Knuth, TAOCP vol. 2,
+//      4.3.1; Moller & Granlund, IEEE TC 60(2), 2011).
 //   3. The 53-bit quotient is rounded to nearest with the remainder
 //      (a binary division can never land exactly half-way) and assembled.
 // ---------------------------------------------------------------------------
@@ -151,24 +151,33 @@ __device__ __forceinline__ F53 round53(uint64_t x) {
   return F53{m, k};
 }
 
-// floor(2^115 / d) up to a few units, d in (2^52, 2^53).
+// floor(2^115 / d) within +-2, d in (2^52, 2^53).  Seed y0 = m24 * 2^s0 from
+// the single-precision reciprocal of d's top 24 bits (relative error < 2^-21),
+// then one third-order step y = y0 (1 + e + e^2), e = 1 - d y0 / 2^115, which
+// leaves a relative error near e^3 < 2^-63.  d*y0 differs from 2^115 by less
+// than 2^(s0+54), so e is exact from the low 64 bits of d*m24.
 __device__ __forceinline__ uint64_t recip115(uint64_t d) {
   const float df = static_cast<float>(static_cast<uint32_t>(d >> 29));  // exact: < 2^24
   float f;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"(df));
   const uint32_t fb = __float_as_uint(f);
-  const int ef = static_cast<int>((fb >> 23) & 0xFFu) - 127;  // -24 or -23
-  uint64_t y = static_cast<uint64_t>((fb & 0x7FFFFFu) | 0x800000u) << (63 + ef);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const uint64_t lo = d * y, hi = __umul64hi(d, y);           // d*y ~ 2^115
-    const int64_t e34 = static_cast<int64_t>(((1ull << 51) - hi) << 30) -
-                        static_cast<int64_t>(lo >> 34);            // (2^115 - d*y) / 2^34
-    const uint64_t ae = static_cast<uint64_t>(e34 < 0 ? -e34 : e34);
-    const uint64_t c = __umul64hi(y, ae) >> 17;                   // y * |e| / 2^115
-    y = e34 < 0 ? y - c : y + c;
-  }
-  return y;
+  const int s0 = static_cast<int>((fb >> 23) & 0xFFu) - 127 + 63;  // 39 or 40
+  const uint32_t m24 = (fb & 0x7FFFFFu) | 0x800000u;
+  // e * 2^(115 - s0) = 2^(115 - s0) - d*m24; the power of two vanishes mod 2^64
+  const int64_t e = -static_cast<int64_t>(d * static_cast<uint64_t>(m24));
+  const uint64_t ae = static_cast<uint64_t>(e < 0 ? -e : e);
+  // t1 = y0 |e| = m24 |e'| / 2^(115 - 2 s0), from the 32-bit halves of |e'|
+  const int sh = 115 - 2 * s0;  // 37 or 35
+  const uint64_t P1 = static_cast<uint64_t>(m24) * static_cast<uint32_t>(ae >> 32);
+  const uint64_t P0 = static_cast<uint64_t>(m24) * static_cast<uint32_t>(ae);
+  const uint64_t t1 =
+      (P1 >> (sh - 32)) + ((((P1 & ((1ull << (sh - 32)) - 1ull)) << 32) + P0) >> sh);
+  // t2 = y0 e^2 = m24 e'^2 / 2^(230 - 3 s0) >= 0, to a fraction of a unit
+  const uint64_t e24 = ae >> 24;            // < 2^30
+  const uint64_t e2 = (e24 * e24) >> 24;    // e'^2 / 2^72
+  const uint64_t t2 = (static_cast<uint64_t>(m24) * e2) >> (158 - 3 * s0);
+  const uint64_t y0 = static_cast<uint64_t>(m24) << s0;
+  return (e >= 0 ? y0 + t1 : y0 - t1) + t2;
 }
 
 // IEEE binary64 RN quotient (E_q58 * 2^-58) / (RN(A) * 2^-32), as a double.

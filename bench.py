@@ -141,7 +141,10 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:  # independent replica per rank
         spec = replace(spec, tissue_id=rank)
     g = Tissue(spec)
-    g.set_launch(args.chi_wpb or DEFAULT_CHI_WPB)
+    if args.kernel == "persistent":
+        g.set_launch_config(1, args.lanes, args.chi_wpb or 4, 0)
+    else:
+        g.set_launch(args.chi_wpb or DEFAULT_CHI_WPB)
     burn = int(round(args.burn_in / args.dt))
     if burn:
         g.step(args.dt, burn)
@@ -245,8 +248,10 @@ def run_ours(args, rank, world, local_rank):
                                "Notch-Delta model",
                    "dt": args.dt, "burn_in_time": args.burn_in, "cells": spec.cells,
                    "voxels_per_cell": spec.V, "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"replicas x{world}", "chi_warps_per_block":
-                   args.chi_wpb or DEFAULT_CHI_WPB},
+                   "parallelism": f"replicas x{world}",
+                   "chi_launch": {"kernel": args.kernel, "lanes_per_cell":
+                                  args.lanes if args.kernel == "persistent" else 32,
+                                  "warps_per_block": args.chi_wpb or DEFAULT_CHI_WPB}},
         "cell_steps_per_s": cell_steps / (total_ms_job / 1e3),
         "events_per_step": events_job / args.steps,
         "chi_ms_per_step": chi_ms / args.steps, "sig_ms_per_step": sig_ms / args.steps,
@@ -323,6 +328,8 @@ def main():
     ap.add_argument("--dt", type=float, default=0.1, choices=[0.01, 0.1, 1.0])
     ap.add_argument("--burn-in", type=float, default=20.0, help="untimed simulated time first")
     ap.add_argument("--chi-wpb", type=int, default=0)
+    ap.add_argument("--kernel", choices=["warp", "persistent"], default="warp")
+    ap.add_argument("--lanes", type=int, choices=[16, 32], default=16)
     ap.add_argument("--chi-traffic", type=float, default=None,
                     help="DRAM bytes per chi launch from an ncu capture, if known")
     ap.add_argument("--ref-side", type=int, default=16)

@@ -139,9 +139,22 @@ int tissue_get_step(const tissue* t, uint32_t* step_index);
 /* Wait for the queued work; report a latched device error. */
 int tissue_sync(tissue* t);
 
-/* Launch shape of the chi kernel: warps (cells) per block, 1..16.
- * Results never depend on it. */
+/* Launch shape of the chi kernel: warps (cells) per block, 1..16, of the
+ * one-warp-per-cell kernel.  Results never depend on it. */
 int tissue_set_launch(tissue* t, uint32_t chi_warps_per_block);
+
+/* Kernel choice for chi.  Results never depend on it: every configuration
+ * computes the same trajectory bit for bit. */
+#define TISSUE_KERNEL_WARP 0u       /* one warp per cell, one launch over all cells */
+#define TISSUE_KERNEL_PERSISTENT 1u /* persistent kernel, cells taken from a work list */
+typedef struct {
+  uint32_t kernel;          /* TISSUE_KERNEL_WARP or TISSUE_KERNEL_PERSISTENT */
+  uint32_t lanes_per_cell;  /* persistent kernel: 32, or 16 (two cells per warp; V <= 256) */
+  uint32_t warps_per_block; /* 1..16 (warp kernel) or 1..8 (persistent kernel) */
+  uint32_t blocks;          /* persistent kernel grid; 0 = enough to fill every SM */
+} tissue_launch;
+int tissue_set_launch_config(tissue* t, const tissue_launch* config);
+int tissue_get_launch_config(const tissue* t, tissue_launch* config);
 
 /* Largest tissue (width*height cells) tissue_step_noalloc accepts. */
 #define TISSUE_NOALLOC_MAX_CELLS 16384

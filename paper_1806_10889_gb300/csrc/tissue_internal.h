@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "tissue.h"
+
 #include <cstddef>
 #include <cstdint>
 
@@ -46,6 +48,16 @@ cudaError_t launch_init(const TissueView& t, const double p0[3], const double la
                         cudaStream_t stream);
 cudaError_t launch_chi(const TissueView& t, uint32_t step_off, double dt, int warps_per_block,
                        cudaStream_t stream);
+// Persistent segmented chi over a work list: d_items = nullptr means the cells
+// of d_views[0] in order.  H = 16 or 32 lanes per cell; vmax_cells is the
+// largest V among the listed tissues (sizes shared memory).  blocks <= 0
+// picks a grid that fills every SM.
+cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
+                           uint32_t* d_counter, uint32_t vmax_cells, int H, int warps_per_block,
+                           int blocks, uint32_t step_off, double dt, cudaStream_t stream);
+uint32_t seg_bytes_for(uint32_t V, int H);
+int seg_lanes_for(uint32_t V, int want);
+
 cudaError_t launch_sig(const TissueView& t, int axis, uint32_t step_off, double dt,
                        cudaStream_t stream);
 cudaError_t launch_step_advance(uint32_t* step, uint32_t n, cudaStream_t stream);

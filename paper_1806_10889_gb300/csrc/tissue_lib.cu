@@ -32,7 +32,9 @@ struct tissue {
   uint32_t* d_step = nullptr;
   int* d_err = nullptr;
   uint32_t step_index = 0;
-  int chi_wpb = 4;
+  tissue_launch cfg{TISSUE_KERNEL_WARP, 32, 4, 0};
+  TissueView* d_view = nullptr;   // device copy of the view, for the persistent kernel
+  uint32_t* d_work = nullptr;     // work-list counter of the persistent kernel
 };
 
 namespace {
@@ -50,7 +52,7 @@ bool desc_ok(const tissue_desc* d) {
 uint64_t cells_of(const tissue_desc* d) { return static_cast<uint64_t>(d->width) * d->height; }
 
 struct ScratchLayout {
-  size_t hill, ev_last, t_last, ev_total, step, err, total;
+  size_t hill, ev_last, t_last, ev_total, step, err, view, work, total;
 };
 
 ScratchLayout layout(const tissue_desc* d) {
@@ -70,6 +72,10 @@ ScratchLayout layout(const tissue_desc* d) {
   o = up(o + sizeof(uint32_t));
   L.err = o;
   o = up(o + sizeof(int));
+  L.view = o;
+  o = up(o + sizeof(TissueView));
+  L.work = o;
+  o = up(o + sizeof(uint32_t));
   L.total = o;
   return L;
 }
@@ -91,6 +97,19 @@ TissueView view_of(const tissue* t) {
   v.step = t->d_step;
   v.err = t->d_err;
   return v;
+}
+
+// chi for step offset i, in the tissue's launch configuration.
+cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt) {
+  const tissue_launch& c = t->cfg;
+  if (c.kernel == TISSUE_KERNEL_PERSISTENT) {
+    cudaError_t e = cudaMemsetAsync(t->d_work, 0, sizeof(uint32_t), t->stream);
+    if (e != cudaSuccess) return e;
+    return launch_chi_seg(t->d_view, nullptr, t->d.width * t->d.height, t->d_work, v.V,
+                          static_cast<int>(c.lanes_per_cell), static_cast<int>(c.warps_per_block),
+                          static_cast<int>(c.blocks), i, dt, t->stream);
+  }
+  return launch_chi(v, i, dt, static_cast<int>(c.warps_per_block), t->stream);
 }
 
 int device_error(tissue* t) {
@@ -175,6 +194,8 @@ int tissue_create(const tissue_desc* d, void* dev_counts, size_t bytes, void* cu
   t->ev_total = reinterpret_cast<uint64_t*>(t->scratch + L.ev_total);
   t->d_step = reinterpret_cast<uint32_t*>(t->scratch + L.step);
   t->d_err = reinterpret_cast<int*>(t->scratch + L.err);
+  t->d_view = reinterpret_cast<TissueView*>(t->scratch + L.view);
+  t->d_work = reinterpret_cast<uint32_t*>(t->scratch + L.work);
   if (cudaMemsetAsync(t->scratch, 0, L.total, t->stream) != cudaSuccess) {
     cudaFree(t->scratch);
     delete t;
@@ -202,6 +223,9 @@ int tissue_set_model(tissue* t, const tissue_model* m) {
   if (!make_qrates(r, t->hill, &q)) return TISSUE_E_ARG;
   if (launch_hill_table(q, t->hill, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
   t->q = q;
+  const TissueView v = view_of(t);
+  if (cudaMemcpyAsync(t->d_view, &v, sizeof(v), cudaMemcpyHostToDevice, t->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
   t->has_model = true;
   return TISSUE_OK;
 }
@@ -231,7 +255,7 @@ int tissue_step(tissue* t, double dt, uint32_t n_steps) {
   if (n_steps == 0) return TISSUE_OK;
   const TissueView v = view_of(t);
   for (uint32_t i = 0; i < n_steps; ++i) {
-    if (launch_chi(v, i, dt, t->chi_wpb, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+    if (launch_chi_cfg(t, v, i, dt) != cudaSuccess) return TISSUE_E_CUDA;
     if (launch_sig(v, 0, i, dt, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
     if (launch_sig(v, 1, i, dt, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
   }
@@ -253,7 +277,7 @@ int tissue_step_timed(tissue* t, double dt, uint32_t n_steps, double* ms_chi, do
   const TissueView v = view_of(t);
   if (rc == TISSUE_OK && cudaEventRecord(marks[0], t->stream) != cudaSuccess) rc = TISSUE_E_CUDA;
   for (uint32_t i = 0; i < n_steps && rc == TISSUE_OK; ++i) {
-    if (launch_chi(v, i, dt, t->chi_wpb, t->stream) != cudaSuccess ||
+    if (launch_chi_cfg(t, v, i, dt) != cudaSuccess ||
         cudaEventRecord(marks[2 * i + 1], t->stream) != cudaSuccess ||
         launch_sig(v, 0, i, dt, t->stream) != cudaSuccess ||
         launch_sig(v, 1, i, dt, t->stream) != cudaSuccess ||
@@ -332,7 +356,32 @@ int tissue_sync(tissue* t) {
 
 int tissue_set_launch(tissue* t, uint32_t chi_warps_per_block) {
   if (!t || chi_warps_per_block < 1 || chi_warps_per_block > 16) return TISSUE_E_ARG;
-  t->chi_wpb = static_cast<int>(chi_warps_per_block);
+  t->cfg = tissue_launch{TISSUE_KERNEL_WARP, 32, chi_warps_per_block, 0};
+  return TISSUE_OK;
+}
+
+int tissue_set_launch_config(tissue* t, const tissue_launch* c) {
+  if (!t || !c) return TISSUE_E_ARG;
+  const uint32_t V = t->d.n * t->d.n;
+  if (c->kernel == TISSUE_KERNEL_WARP) {
+    if (c->warps_per_block < 1 || c->warps_per_block > 16) return TISSUE_E_ARG;
+  } else if (c->kernel == TISSUE_KERNEL_PERSISTENT) {
+    if (c->lanes_per_cell != 32 && c->lanes_per_cell != 16) return TISSUE_E_ARG;
+    if (c->lanes_per_cell == 16 && V > 256) return TISSUE_E_ARG;
+    if (c->warps_per_block < 1 || c->warps_per_block > 8) return TISSUE_E_ARG;
+    if (static_cast<size_t>(c->warps_per_block) * (32 / c->lanes_per_cell) *
+            seg_bytes_for(V, static_cast<int>(c->lanes_per_cell)) > 227 * 1024)
+      return TISSUE_E_ARG;
+  } else {
+    return TISSUE_E_ARG;
+  }
+  t->cfg = *c;
+  return TISSUE_OK;
+}
+
+int tissue_get_launch_config(const tissue* t, tissue_launch* c) {
+  if (!t || !c) return TISSUE_E_ARG;
+  *c = t->cfg;
   return TISSUE_OK;
 }
 

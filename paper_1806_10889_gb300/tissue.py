@@ -46,6 +46,14 @@ class Model(C.Structure):
     _fields_ = [(f, C.c_double) for f in MODEL_FIELDS]
 
 
+KERNEL_WARP, KERNEL_PERSISTENT = 0, 1
+
+
+class Launch(C.Structure):
+    _fields_ = [("kernel", C.c_uint32), ("lanes_per_cell", C.c_uint32),
+                ("warps_per_block", C.c_uint32), ("blocks", C.c_uint32)]
+
+
 # Every exported symbol of include/tissue.h with (restype, argtypes).
 _P = C.POINTER
 SIGNATURES = {
@@ -63,6 +71,8 @@ SIGNATURES = {
     "tissue_get_step": (C.c_int, [C.c_void_p, _P(C.c_uint32)]),
     "tissue_sync": (C.c_int, [C.c_void_p]),
     "tissue_set_launch": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "tissue_set_launch_config": (C.c_int, [C.c_void_p, _P(Launch)]),
+    "tissue_get_launch_config": (C.c_int, [C.c_void_p, _P(Launch)]),
     "tissue_step_noalloc": (C.c_int, [_P(Desc), _P(Model), C.c_void_p, C.c_uint32, C.c_double,
                                       C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tissue_selftest_time": (C.c_int, [C.c_uint64, C.c_uint64, _P(C.c_uint64)]),
@@ -176,6 +186,16 @@ class Tissue:
 
     def set_launch(self, chi_warps_per_block: int):
         _check(lib().tissue_set_launch(self._h, int(chi_warps_per_block)), "tissue_set_launch")
+
+    def set_launch_config(self, kernel: int, lanes_per_cell: int = 32, warps_per_block: int = 4,
+                          blocks: int = 0):
+        c = Launch(kernel, lanes_per_cell, warps_per_block, blocks)
+        _check(lib().tissue_set_launch_config(self._h, C.byref(c)), "tissue_set_launch_config")
+
+    def launch_config(self) -> tuple:
+        c = Launch()
+        _check(lib().tissue_get_launch_config(self._h, C.byref(c)), "tissue_get_launch_config")
+        return (c.kernel, c.lanes_per_cell, c.warps_per_block, c.blocks)
 
     def step(self, dt: float, n_steps: int = 1):
         _check(lib().tissue_step(self._h, float(dt), int(n_steps)), "tissue_step")

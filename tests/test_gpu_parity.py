@@ -38,12 +38,15 @@ def _compare_step(g: Tissue, d, counts, ne, tl, ctx=""):
     assert np.array_equal(_bits(gtl), _bits(tl)), f"{ctx}: event times differ"
 
 
-def _run_both(spec: TissueSpec, dt: float, n_steps: int, wpb: int | None = None, every=True):
+def _run_both(spec: TissueSpec, dt: float, n_steps: int, wpb: int | None = None, every=True,
+              config: tuple | None = None):
     d, m = orc_desc(spec), orc_model(spec)
     counts = O.init_counts(d)
     g = Tissue(spec)
     if wpb:
         g.set_launch(wpb)
+    if config:
+        g.set_launch_config(*config)
     assert np.array_equal(g.read_counts(), counts), "initial counts differ"
     for k in range(n_steps):
         ne, tl = O.step(d, m, counts, k, 1, dt)
@@ -92,9 +95,45 @@ def test_launch_shape_does_not_change_results(wpb):
     _run_both(spec, 0.1, 2, wpb=wpb, every=False)
 
 
-def test_in_voxel_binding_channels():
+PERSISTENT = [(T.KERNEL_PERSISTENT, 32, 4, 0), (T.KERNEL_PERSISTENT, 16, 4, 0),
+              (T.KERNEL_PERSISTENT, 16, 2, 1), (T.KERNEL_PERSISTENT, 32, 1, 3)]
+
+
+@pytest.mark.parametrize("config", PERSISTENT)
+@pytest.mark.parametrize("w,h,n,dt", [
+    (5, 3, 16, 0.1), (3, 2, 10, 0.1), (4, 1, 2, 0.5), (1, 3, 7, 0.2), (7, 5, 8, 1.0),
+    (2, 2, 32, 0.05),
+])
+def test_persistent_kernel_matches_oracle(config, w, h, n, dt):
+    """The persistent work-list kernel, one or two cells per warp, any grid
+    (down to a single block pulling every cell), gives the oracle's bits."""
+    if config[1] == 16 and n * n > 256:
+        pytest.skip("16 lanes per cell need V <= 256")
+    spec = TissueSpec(w, h, n, seed=2000 + w * 100 + n, tissue_id=w * h).with_model(**STRONG)
+    _run_both(spec, dt, 3, config=config)
+
+
+def test_persistent_kernel_medium_tissue():
+    run = W.medium(0.1)
+    _run_both(run.tissue, run.dt, 2, config=(T.KERNEL_PERSISTENT, 16, 4, 0))
+
+
+def test_launch_config_validation():
+    g = Tissue(TissueSpec(2, 2, 32, seed=1))
+    with pytest.raises(T.TissueError):
+        g.set_launch_config(T.KERNEL_PERSISTENT, 16, 4, 0)  # V = 1024 needs 32 lanes
+    with pytest.raises(T.TissueError):
+        g.set_launch_config(7, 32, 4, 0)
+    g.set_launch_config(T.KERNEL_PERSISTENT, 32, 2, 0)
+    assert g.launch_config() == (T.KERNEL_PERSISTENT, 32, 2, 0)
+    g.close()
+
+
+@pytest.mark.parametrize("config", [None, (T.KERNEL_PERSISTENT, 16, 4, 0),
+                                    (T.KERNEL_PERSISTENT, 32, 4, 0)])
+def test_in_voxel_binding_channels(config):
     spec = TissueSpec(3, 3, 6, seed=17).with_model(k_in=0.02, k_off=0.7)
-    _run_both(spec, 0.2, 4)
+    _run_both(spec, 0.2, 4, config=config)
 
 
 def test_medium_config_full_tissue():
@@ -192,9 +231,12 @@ def test_rerun_is_bit_identical_and_totals_add_up():
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
 
 
-def test_overflow_is_reported():
+@pytest.mark.parametrize("config", [None, (T.KERNEL_PERSISTENT, 16, 4, 0)])
+def test_overflow_is_reported(config):
     spec = TissueSpec(2, 1, 2, seed=1, init_lambda=(0.0, 0.0, 0.0)).with_model(hopD=1000.0)
     g = Tissue(spec)
+    if config:
+        g.set_launch_config(*config)
     x = np.zeros(spec.state_ints, dtype=np.int32)
     x[0] = 2 ** 30 - 1
     g.write_counts(x)

@@ -143,8 +143,9 @@ def run_ours(args, rank, world, local_rank):
     g = Tissue(spec)
     if args.kernel == "persistent":
         g.set_launch_config(1, args.lanes, args.chi_wpb or 4, 0)
-    else:
+    elif args.kernel == "warp":
         g.set_launch(args.chi_wpb or DEFAULT_CHI_WPB)
+    launch = g.launch_config()
     burn = int(round(args.burn_in / args.dt))
     if burn:
         g.step(args.dt, burn)
@@ -249,9 +250,8 @@ def run_ours(args, rank, world, local_rank):
                    "dt": args.dt, "burn_in_time": args.burn_in, "cells": spec.cells,
                    "voxels_per_cell": spec.V, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}",
-                   "chi_launch": {"kernel": args.kernel, "lanes_per_cell":
-                                  args.lanes if args.kernel == "persistent" else 32,
-                                  "warps_per_block": args.chi_wpb or DEFAULT_CHI_WPB}},
+                   "chi_launch": {"kernel": ["warp", "persistent"][launch[0]],
+                                  "lanes_per_cell": launch[1], "warps_per_block": launch[2]}},
         "cell_steps_per_s": cell_steps / (total_ms_job / 1e3),
         "events_per_step": events_job / args.steps,
         "chi_ms_per_step": chi_ms / args.steps, "sig_ms_per_step": sig_ms / args.steps,
@@ -328,7 +328,7 @@ def main():
     ap.add_argument("--dt", type=float, default=0.1, choices=[0.01, 0.1, 1.0])
     ap.add_argument("--burn-in", type=float, default=20.0, help="untimed simulated time first")
     ap.add_argument("--chi-wpb", type=int, default=0)
-    ap.add_argument("--kernel", choices=["warp", "persistent"], default="warp")
+    ap.add_argument("--kernel", choices=["default", "warp", "persistent"], default="default")
     ap.add_argument("--lanes", type=int, choices=[16, 32], default=16)
     ap.add_argument("--chi-traffic", type=float, default=None,
                     help="DRAM bytes per chi launch from an ncu capture, if known")

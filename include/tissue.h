@@ -153,8 +153,50 @@ typedef struct {
   uint32_t warps_per_block; /* 1..16 (warp kernel) or 1..8 (persistent kernel) */
   uint32_t blocks;          /* persistent kernel grid; 0 = enough to fill every SM */
 } tissue_launch;
+/* The default after tissue_create: persistent, 16 lanes, 4 warps per block for
+ * cells of at most 256 voxels; otherwise the warp kernel, 4 warps per block. */
 int tissue_set_launch_config(tissue* t, const tissue_launch* config);
 int tissue_get_launch_config(const tissue* t, tissue_launch* config);
+
+/* ---- Batching: many tissues in one persistent launch per step ----------
+ * The members keep their own buffers, models, statistics and step indices;
+ * one batch step runs chi for the cells of every member with the persistent
+ * kernel (one launch per cell-size class, cells taken from a work list),
+ * then all members' x-faces, then all y-faces, then advances every member's
+ * step index.  The step is captured in a CUDA graph on first use (per dt) and
+ * replayed.  Each tissue's trajectory is bit-identical to stepping it alone.
+ * While a batch exists, step its members only through it; a member's model
+ * must not change (recreate the batch instead).  The members must outlive
+ * the batch. */
+typedef struct tissue_batch tissue_batch;
+
+/* count >= 1 distinct tissues with models set, on the current device.
+ * cuda_stream: the stream batch steps run on (NULL = legacy default stream,
+ * which is not graph-captured).  Waits for the members' pending work. */
+int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_stream,
+                        tissue_batch** out);
+
+/* Launch shape of the chi launch of the class of cells with V voxels:
+ * 16 (V <= 256) or 32 lanes per cell, 1..8 warps per block.  The default is
+ * 16 lanes where allowed, 4 warps per block.  Results never depend on it. */
+int tissue_batch_set_class_launch(tissue_batch* b, uint32_t V, uint32_t lanes_per_cell,
+                                  uint32_t warps_per_block);
+
+/* Split-step schedule: how many splitting steps one captured graph holds
+ * (1..64, default 1); n_steps not divisible by it end with direct launches. */
+int tissue_batch_set_schedule(tissue_batch* b, uint32_t steps_per_graph);
+
+/* Enqueue n_steps batch steps of length dt on the batch stream. */
+int tissue_batch_step(tissue_batch* b, double dt, uint32_t n_steps);
+
+/* Wait for the batch stream; report the first member's latched device error. */
+int tissue_batch_sync(tissue_batch* b);
+
+/* Members, cell-size classes and total cells of the batch (any may be NULL). */
+int tissue_batch_info(const tissue_batch* b, uint32_t* n_members, uint32_t* n_classes,
+                      uint64_t* n_cells);
+
+void tissue_batch_destroy(tissue_batch* b);
 
 /* Largest tissue (width*height cells) tissue_step_noalloc accepts. */
 #define TISSUE_NOALLOC_MAX_CELLS 16384

@@ -20,14 +20,11 @@ namespace tsg {
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_sig(const TissueView t, const int axis,
-                                             const uint32_t step_off, const double dt) {
+// The face owned by cell c on `axis`, advanced over [0, dt) by one warp.
+__device__ __forceinline__ void sig_face(const TissueView& t, const uint32_t c, const int axis,
+                                         const uint32_t step_off, const double dt) {
   const int lane = threadIdx.x & 31;
   const uint32_t W = t.width, H = t.height;
-  const uint32_t nfaces = axis == 0 ? (W - 1) * H : W * (H - 1);
-  const uint32_t f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (f >= nfaces) return;  // whole warp
-  const uint32_t c = axis == 0 ? (f / (W - 1)) * W + f % (W - 1) : f;
   const uint32_t nb = axis == 0 ? c + 1 : c + W;
   const int n = static_cast<int>(t.n), V = static_cast<int>(t.V);
   int32_t* ga = t.counts + static_cast<size_t>(c) * 3 * V;
@@ -137,6 +134,32 @@ __global__ void __launch_bounds__(256) k_sig(const TissueView t, const int axis,
   }
 }
 
+__global__ void __launch_bounds__(256) k_sig(const TissueView t, const int axis,
+                                             const uint32_t step_off, const double dt) {
+  const uint32_t W = t.width, H = t.height;
+  const uint32_t nfaces = axis == 0 ? (W - 1) * H : W * (H - 1);
+  const uint32_t f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (f >= nfaces) return;  // whole warp
+  sig_face(t, axis == 0 ? (f / (W - 1)) * W + f % (W - 1) : f, axis, step_off, dt);
+}
+
+// Faces of many tissues: item = (tissue index, owner cell).
+__global__ void __launch_bounds__(256) k_sig_list(const TissueView* __restrict__ views,
+                                                  const uint2* __restrict__ items,
+                                                  const uint32_t n_items, const int axis,
+                                                  const double dt) {
+  const uint32_t f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (f >= n_items) return;  // whole warp
+  const uint2 w = items[f];
+  sig_face(views[w.x], w.y, axis, 0u, dt);
+}
+
+// Advance the step counter of every tissue of a batch by one.
+__global__ void k_advance_list(const TissueView* __restrict__ views, const uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) *const_cast<uint32_t*>(views[i].step) += 1u;
+}
+
 // Initial counts: Poisson(lambda_s) per voxel and species by inversion,
 // accumulating p_k = p_{k-1} * lambda / k; p0 = exp(-lambda) from the host.
 __global__ void k_init(const TissueView t, const double p0_0, const double p0_1, const double p0_2,
@@ -183,6 +206,21 @@ cudaError_t launch_sig(const TissueView& t, int axis, uint32_t step_off, double 
   if (nfaces == 0) return cudaSuccess;
   constexpr int kWarps = 8;
   k_sig<<<(nfaces + kWarps - 1) / kWarps, 32 * kWarps, 0, stream>>>(t, axis, step_off, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sig_list(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
+                            int axis, double dt, cudaStream_t stream) {
+  if (n_items == 0) return cudaSuccess;
+  constexpr int kWarps = 8;
+  k_sig_list<<<(n_items + kWarps - 1) / kWarps, 32 * kWarps, 0, stream>>>(d_views, d_items, n_items,
+                                                                         axis, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_list(const TissueView* d_views, uint32_t n, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  k_advance_list<<<(n + 255) / 256, 256, 0, stream>>>(d_views, n);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,267 @@
+// tissue_batch: many tissues advanced by one persistent launch per step.
+//
+// Each member keeps its own state buffer, statistics and step counter; the
+// batch holds a device table of the members' views, the chi work list of
+// every cell-size class (V) and the face lists of both phases.  One
+// splitting step is: for every class, the persistent chi kernel over the
+// class's (tissue, cell) items; then one face kernel over all x-faces of all
+// members, one over all y-faces; then every member's step counter advances.
+// The step is captured once in a CUDA graph per dt and replayed, so a batch
+// step costs a handful of graph launches regardless of how many tissues it
+// holds.  Work items never enter the random streams (which are keyed by a
+// tissue's seed, id, cell and step), so a tissue's trajectory is the same
+// alone and in any batch.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "tissue.h"
+#include "tissue_internal.h"
+
+using namespace tsg;
+
+namespace {
+
+struct ClassPlan {
+  uint32_t V;
+  uint32_t lanes, warps_per_block;
+  size_t items_off;  // offset (in uint2) into the item buffer
+  uint32_t n_items;
+};
+
+}  // namespace
+
+struct tissue_batch {
+  std::vector<tissue*> members;
+  cudaStream_t stream = nullptr;
+  std::vector<ClassPlan> classes;
+  unsigned char* dmem = nullptr;
+  TissueView* d_views = nullptr;
+  uint2* d_items = nullptr;   // chi items of every class, then x-faces, then y-faces
+  uint32_t* d_counters = nullptr;
+  size_t xface_off = 0, yface_off = 0;
+  uint32_t n_xfaces = 0, n_yfaces = 0;
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
+  uint32_t steps_per_graph = 1;
+};
+
+namespace {
+
+int enqueue_step(tissue_batch* b, double dt) {
+  for (size_t c = 0; c < b->classes.size(); ++c) {
+    const ClassPlan& p = b->classes[c];
+    if (cudaMemsetAsync(b->d_counters + c, 0, sizeof(uint32_t), b->stream) != cudaSuccess)
+      return TISSUE_E_CUDA;
+    if (launch_chi_seg(b->d_views, b->d_items + p.items_off, p.n_items, b->d_counters + c, p.V,
+                       static_cast<int>(p.lanes), static_cast<int>(p.warps_per_block), 0, 0u, dt,
+                       b->stream) != cudaSuccess)
+      return TISSUE_E_CUDA;
+  }
+  if (launch_sig_list(b->d_views, b->d_items + b->xface_off, b->n_xfaces, 0, dt, b->stream) !=
+          cudaSuccess ||
+      launch_sig_list(b->d_views, b->d_items + b->yface_off, b->n_yfaces, 1, dt, b->stream) !=
+          cudaSuccess ||
+      launch_advance_list(b->d_views, static_cast<uint32_t>(b->members.size()), b->stream) !=
+          cudaSuccess)
+    return TISSUE_E_CUDA;
+  return TISSUE_OK;
+}
+
+void drop_graph(tissue_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_stream,
+                        tissue_batch** out) {
+  if (!out) return TISSUE_E_ARG;
+  *out = nullptr;
+  if (!members || count == 0) return TISSUE_E_ARG;
+  std::vector<TissueInfo> info(count);
+  for (uint32_t i = 0; i < count; ++i) {
+    if (!tissue_info(members[i], &info[i])) return TISSUE_E_ARG;
+    if (!info[i].has_model) return TISSUE_E_NOMODEL;
+    for (uint32_t j = 0; j < i; ++j)
+      if (members[j] == members[i]) return TISSUE_E_ARG;  // a tissue may appear once
+  }
+  tissue_batch* b = new (std::nothrow) tissue_batch();
+  if (!b) return TISSUE_E_NOMEM;
+  b->members.assign(members, members + count);
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+
+  // chi items by class, largest cells first; faces of both phases
+  std::map<uint32_t, std::vector<uint2>, std::greater<uint32_t>> by_v;
+  std::vector<uint2> xf, yf;
+  for (uint32_t i = 0; i < count; ++i) {
+    const tissue_desc& d = info[i].desc;
+    const uint32_t V = d.n * d.n, cells = d.width * d.height;
+    std::vector<uint2>& list = by_v[V];
+    for (uint32_t c = 0; c < cells; ++c) list.push_back(make_uint2(i, c));
+    for (uint32_t c = 0; c < cells; ++c) {
+      const uint32_t cx = c % d.width, cy = c / d.width;
+      if (cx + 1 < d.width) xf.push_back(make_uint2(i, c));
+      if (cy + 1 < d.height) yf.push_back(make_uint2(i, c));
+    }
+  }
+  std::vector<uint2> items;
+  for (auto& kv : by_v) {
+    ClassPlan p{};
+    p.V = kv.first;
+    p.lanes = kv.first <= 256 ? 16u : 32u;
+    p.warps_per_block = 4;
+    p.items_off = items.size();
+    p.n_items = static_cast<uint32_t>(kv.second.size());
+    items.insert(items.end(), kv.second.begin(), kv.second.end());
+    b->classes.push_back(p);
+  }
+  b->xface_off = items.size();
+  b->n_xfaces = static_cast<uint32_t>(xf.size());
+  items.insert(items.end(), xf.begin(), xf.end());
+  b->yface_off = items.size();
+  b->n_yfaces = static_cast<uint32_t>(yf.size());
+  items.insert(items.end(), yf.begin(), yf.end());
+
+  const size_t views_bytes = (sizeof(TissueView) * count + 255) & ~static_cast<size_t>(255);
+  const size_t items_bytes = (sizeof(uint2) * items.size() + 255) & ~static_cast<size_t>(255);
+  const size_t total = views_bytes + items_bytes + sizeof(uint32_t) * b->classes.size();
+  if (cudaMalloc(&b->dmem, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return TISSUE_E_NOMEM;
+  }
+  b->d_views = reinterpret_cast<TissueView*>(b->dmem);
+  b->d_items = reinterpret_cast<uint2*>(b->dmem + views_bytes);
+  b->d_counters = reinterpret_cast<uint32_t*>(b->dmem + views_bytes + items_bytes);
+  std::vector<TissueView> views(count);
+  for (uint32_t i = 0; i < count; ++i) views[i] = info[i].view;
+  // Members' pending work (creation, earlier steps) must finish before the
+  // batch stream uses their buffers.
+  for (uint32_t i = 0; i < count; ++i)
+    if (cudaStreamSynchronize(info[i].stream) != cudaSuccess) {
+      cudaFree(b->dmem);
+      delete b;
+      return TISSUE_E_CUDA;
+    }
+  if (cudaMemcpy(b->d_views, views.data(), sizeof(TissueView) * count, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(b->d_items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaFree(b->dmem);
+    delete b;
+    return TISSUE_E_CUDA;
+  }
+  *out = b;
+  return TISSUE_OK;
+}
+
+int tissue_batch_set_class_launch(tissue_batch* b, uint32_t V, uint32_t lanes_per_cell,
+                                  uint32_t warps_per_block) {
+  if (!b) return TISSUE_E_ARG;
+  if (lanes_per_cell != 16 && lanes_per_cell != 32) return TISSUE_E_ARG;
+  if (lanes_per_cell == 16 && V > 256) return TISSUE_E_ARG;
+  if (warps_per_block < 1 || warps_per_block > 8) return TISSUE_E_ARG;
+  if (static_cast<size_t>(warps_per_block) * (32 / lanes_per_cell) *
+          seg_bytes_for(V, static_cast<int>(lanes_per_cell)) > 227 * 1024)
+    return TISSUE_E_ARG;
+  for (ClassPlan& p : b->classes)
+    if (p.V == V) {
+      p.lanes = lanes_per_cell;
+      p.warps_per_block = warps_per_block;
+      drop_graph(b);
+      return TISSUE_OK;
+    }
+  return TISSUE_E_ARG;
+}
+
+int tissue_batch_step(tissue_batch* b, double dt, uint32_t n_steps) {
+  if (!b) return TISSUE_E_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return TISSUE_E_ARG;
+  if (n_steps == 0) return TISSUE_OK;
+  if (!b->graph || b->graph_dt != dt) {
+    drop_graph(b);
+    // A legacy default stream cannot be captured: fall back to direct launches.
+    if (b->stream == nullptr) {
+      for (uint32_t s = 0; s < n_steps; ++s) {
+        const int rc = enqueue_step(b, dt);
+        if (rc != TISSUE_OK) return rc;
+      }
+      for (tissue* m : b->members) tissue_advance_host_step(m, n_steps);
+      return TISSUE_OK;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return TISSUE_E_CUDA;
+    int rc = TISSUE_OK;
+    for (uint32_t s = 0; s < b->steps_per_graph && rc == TISSUE_OK; ++s) rc = enqueue_step(b, dt);
+    const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+    if (rc != TISSUE_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return TISSUE_E_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      b->graph = nullptr;
+      return TISSUE_E_CUDA;
+    }
+    b->graph_dt = dt;
+  }
+  // whole graphs, then single steps for the remainder
+  const uint32_t k = b->steps_per_graph;
+  for (uint32_t s = 0; s + k <= n_steps; s += k)
+    if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  for (uint32_t s = n_steps - n_steps % k; s < n_steps; ++s) {
+    const int rc = enqueue_step(b, dt);
+    if (rc != TISSUE_OK) return rc;
+  }
+  for (tissue* m : b->members) tissue_advance_host_step(m, n_steps);
+  return TISSUE_OK;
+}
+
+int tissue_batch_set_schedule(tissue_batch* b, uint32_t steps_per_graph) {
+  if (!b || steps_per_graph < 1 || steps_per_graph > 64) return TISSUE_E_ARG;
+  if (steps_per_graph != b->steps_per_graph) drop_graph(b);
+  b->steps_per_graph = steps_per_graph;
+  return TISSUE_OK;
+}
+
+int tissue_batch_sync(tissue_batch* b) {
+  if (!b) return TISSUE_E_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  int worst = TISSUE_OK;
+  for (tissue* m : b->members) {
+    const int rc = tissue_sync(m);
+    if (rc != TISSUE_OK) worst = rc;
+  }
+  return worst;
+}
+
+int tissue_batch_info(const tissue_batch* b, uint32_t* n_members, uint32_t* n_classes,
+                      uint64_t* n_cells) {
+  if (!b) return TISSUE_E_ARG;
+  if (n_members) *n_members = static_cast<uint32_t>(b->members.size());
+  if (n_classes) *n_classes = static_cast<uint32_t>(b->classes.size());
+  if (n_cells) {
+    uint64_t s = 0;
+    for (const ClassPlan& p : b->classes) s += p.n_items;
+    *n_cells = s;
+  }
+  return TISSUE_OK;
+}
+
+void tissue_batch_destroy(tissue_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  cudaFree(b->dmem);
+  delete b;
+}
+
+}  // extern "C"

@@ -56,6 +56,19 @@ cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint
                            uint32_t* d_counter, uint32_t vmax_cells, int H, int warps_per_block,
                            int blocks, uint32_t step_off, double dt, cudaStream_t stream);
 uint32_t seg_bytes_for(uint32_t V, int H);
+cudaError_t launch_sig_list(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
+                            int axis, double dt, cudaStream_t stream);
+cudaError_t launch_advance_list(const TissueView* d_views, uint32_t n, cudaStream_t stream);
+
+// Library-internal access to a tissue handle (tissue_lib.cu).
+struct TissueInfo {
+  tissue_desc desc;
+  TissueView view;
+  cudaStream_t stream;
+  bool has_model;
+};
+bool tissue_info(const tissue* t, TissueInfo* out);
+void tissue_advance_host_step(tissue* t, uint32_t n);
 int seg_lanes_for(uint32_t V, int want);
 
 cudaError_t launch_sig(const TissueView& t, int axis, uint32_t step_off, double dt,

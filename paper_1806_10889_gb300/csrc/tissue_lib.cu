@@ -157,6 +157,17 @@ bool tsg::make_qrates(const double r[12], const uint64_t* hill, QRates* q) {
   return true;
 }
 
+bool tsg::tissue_info(const tissue* t, TissueInfo* out) {
+  if (!t || !out) return false;
+  out->desc = t->d;
+  out->view = view_of(t);
+  out->stream = t->stream;
+  out->has_model = t->has_model;
+  return true;
+}
+
+void tsg::tissue_advance_host_step(tissue* t, uint32_t n) { t->step_index += n; }
+
 extern "C" {
 
 size_t tissue_state_bytes(const tissue_desc* d) {
@@ -182,6 +193,9 @@ int tissue_create(const tissue_desc* d, void* dev_counts, size_t bytes, void* cu
   t->counts = static_cast<int32_t*>(dev_counts);
   t->bytes = bytes;
   t->stream = static_cast<cudaStream_t>(cuda_stream);
+  // Default chi launch: two cells per warp on the persistent kernel where a
+  // cell fits 16 lanes (V <= 256), otherwise one warp per cell.
+  if (d->n * d->n <= 256) t->cfg = tissue_launch{TISSUE_KERNEL_PERSISTENT, 16, 4, 0};
   const ScratchLayout L = layout(d);
   if (cudaMalloc(&t->scratch, L.total) != cudaSuccess) {
     cudaGetLastError();

@@ -76,6 +76,13 @@ SIGNATURES = {
     "tissue_step_noalloc": (C.c_int, [_P(Desc), _P(Model), C.c_void_p, C.c_uint32, C.c_double,
                                       C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tissue_selftest_time": (C.c_int, [C.c_uint64, C.c_uint64, _P(C.c_uint64)]),
+    "tissue_batch_create": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, _P(C.c_void_p)]),
+    "tissue_batch_set_class_launch": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32]),
+    "tissue_batch_step": (C.c_int, [C.c_void_p, C.c_double, C.c_uint32]),
+    "tissue_batch_set_schedule": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "tissue_batch_sync": (C.c_int, [C.c_void_p]),
+    "tissue_batch_info": (C.c_int, [C.c_void_p, _P(C.c_uint32), _P(C.c_uint32), _P(C.c_uint64)]),
+    "tissue_batch_destroy": (None, [C.c_void_p]),
     "tissue_destroy": (None, [C.c_void_p]),
     "tissue_strerror": (C.c_char_p, [C.c_int]),
 }

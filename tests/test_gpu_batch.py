@@ -1,0 +1,106 @@
+"""Batched stepping: many tissues of different sizes and models advance in one
+persistent launch per step (captured in a CUDA graph) and every member ends
+bit-identical to the oracle and to stepping it alone."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_10889_gb300 import workloads as W
+from paper_1806_10889_gb300.workloads import TissueSpec
+from tests._util import orc_desc, orc_model
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1806_10889_gb300 import tissue as T  # noqa: E402
+from paper_1806_10889_gb300.batching import Batch  # noqa: E402
+
+
+def _bits(x):
+    return np.asarray(x, dtype=np.float64).view(np.uint64)
+
+
+MIX = [TissueSpec(3, 2, 8, seed=3, tissue_id=0).with_model(kD=7.5),
+       TissueSpec(5, 4, 16, seed=3, tissue_id=1).with_model(kD=12.0, k_bind=0.05),
+       TissueSpec(2, 2, 32, seed=3, tissue_id=2),
+       TissueSpec(1, 1, 8, seed=3, tissue_id=3),
+       TissueSpec(4, 1, 10, seed=9, tissue_id=4).with_model(k_in=0.01, k_off=0.3),
+       TissueSpec(2, 3, 16, seed=3, tissue_id=5).with_model(kD=19.0)]
+
+
+@pytest.mark.parametrize("steps_per_graph", [1, 2])
+def test_batch_matches_oracle_per_member(steps_per_graph):
+    members = [T.Tissue(s) for s in MIX]
+    b = Batch(members)
+    b.set_schedule(steps_per_graph)
+    assert b.info() == (len(MIX), 4, sum(s.cells for s in MIX))
+    ref = [O.init_counts(orc_desc(s)) for s in MIX]
+    dt = 0.1
+    for k in range(3):
+        b.step(dt, 1)
+        b.sync()
+        for i, s in enumerate(MIX):
+            ne, tl = O.step(orc_desc(s), orc_model(s), ref[i], k, 1, dt)
+            assert np.array_equal(members[i].read_counts(), ref[i]), (k, i)
+            gne, gtl = members[i].read_stats()
+            assert np.array_equal(gne, ne) and np.array_equal(_bits(gtl), _bits(tl)), (k, i)
+    assert all(m.get_step() == 3 for m in members)
+    b.close()
+    for m in members:
+        m.close()
+
+
+def test_batch_class_launch_shapes_give_the_same_bits():
+    results = []
+    for lanes, wpb in ((16, 4), (32, 2), (16, 1), (32, 8)):
+        members = [T.Tissue(s) for s in MIX]
+        b = Batch(members)
+        for V in {s.V for s in MIX}:
+            if lanes == 16 and V > 256:
+                continue
+            b.set_class_launch(V, lanes, wpb)
+        b.step(0.2, 4)
+        b.sync()
+        results.append([m.read_counts() for m in members])
+        b.close()
+        for m in members:
+            m.close()
+    for r in results[1:]:
+        assert all(np.array_equal(a, c) for a, c in zip(results[0], r))
+
+
+def test_batch_workload_members_same_alone_and_in_the_mix():
+    """The benchmark's uneven batch (side 2..64, n in {8,16,32}, kD per tissue):
+    sampled members stepped alone reproduce their in-batch result exactly."""
+    runs = W.batch()
+    members = [T.Tissue(r.tissue) for r in runs]
+    b = Batch(members)
+    b.step(0.1, 2)
+    b.sync()
+    for i in (0, 7, 100, 255):
+        alone = T.Tissue(runs[i].tissue)
+        alone.step(0.1, 2)
+        assert np.array_equal(alone.read_counts(), members[i].read_counts()), i
+        ne_a, tl_a = alone.read_stats()
+        ne_b, tl_b = members[i].read_stats()
+        assert np.array_equal(ne_a, ne_b) and np.array_equal(_bits(tl_a), _bits(tl_b)), i
+        alone.close()
+    b.close()
+    for m in members:
+        m.close()
+
+
+def test_batch_rejects_bad_input():
+    a = T.Tissue(MIX[0])
+    with pytest.raises(T.TissueError):
+        Batch([a, a])
+    b = Batch([a])
+    with pytest.raises(T.TissueError):
+        b.set_class_launch(64, 16, 99)
+    with pytest.raises(T.TissueError):
+        b.set_class_launch(1024, 16, 4)  # no such class
+    b.close()
+    a.close()

@@ -113,11 +113,6 @@ def test_persistent_kernel_matches_oracle(config, w, h, n, dt):
     _run_both(spec, dt, 3, config=config)
 
 
-def test_persistent_kernel_medium_tissue():
-    run = W.medium(0.1)
-    _run_both(run.tissue, run.dt, 2, config=(T.KERNEL_PERSISTENT, 16, 4, 0))
-
-
 def test_launch_config_validation():
     g = Tissue(TissueSpec(2, 2, 32, seed=1))
     with pytest.raises(T.TissueError):
@@ -136,10 +131,12 @@ def test_in_voxel_binding_channels(config):
     _run_both(spec, 0.2, 4, config=config)
 
 
-def test_medium_config_full_tissue():
-    """64x64 cells of 16x16 voxels at dt = 0.1: the whole tissue, two steps."""
+@pytest.mark.parametrize("config", [None, (T.KERNEL_WARP, 32, 4, 0)])
+def test_medium_config_full_tissue(config):
+    """64x64 cells of 16x16 voxels at dt = 0.1: the whole tissue, two steps,
+    in the default launch shape (the benchmark's) and the warp kernel."""
     run = W.medium(0.1)
-    _run_both(run.tissue, run.dt, 2)
+    _run_both(run.tissue, run.dt, 2, config=config)
 
 
 def _neighbourhood_reference(d, m, c, dt):
@@ -177,8 +174,7 @@ def test_large_config_sampled_cells():
     run = W.large()
     spec = run.tissue
     d, m = orc_desc(spec), orc_model(spec)
-    g = Tissue(spec)
-    g.set_launch(T.DEFAULT_CHI_WPB)
+    g = Tissue(spec)  # default launch shape, as the benchmark uses
     g.step(run.dt, 1)
     got = g.read_counts()
     gne, gtl = g.read_stats()

@@ -262,12 +262,113 @@ def run_ours(args, rank, world, local_rank):
         "wall_s_timed": wall,
     }
     g.close()
+    if rank == 0 and not args.no_batch:
+        out["batched"] = batch_leg(args)
+    if rank == 0 and args.serving:
+        out["serving"] = serving_leg(args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+def batch_leg(args) -> dict:
+    """The uneven 256-tissue batch: one persistent launch per cell-size class
+    and step (graph-captured, autotuned) against the plain per-tissue launch
+    (every tissue stepped by its own tissue_step call).  Both legs start from
+    the same state and must end bit-identical."""
+    import torch
+
+    from paper_1806_10889_gb300 import autotune
+    from paper_1806_10889_gb300.batching import Batch
+    from paper_1806_10889_gb300.tissue import Tissue
+
+    runs = W.batch()
+    dt, K = runs[0].dt, args.batch_steps
+    cells = sum(r.tissue.cells for r in runs)
+    plain = [Tissue(r.tissue) for r in runs]
+    for t in plain:
+        t.step(dt, 1)
+    torch.cuda.synchronize()
+    ev0 = sum(int(t.total_events().sum()) for t in plain)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(K):
+        for t in plain:
+            t.step(dt, 1)
+    b.record(stream)
+    b.synchronize()
+    plain_ms = a.elapsed_time(b)
+    plain_events = sum(int(t.total_events().sum()) for t in plain) - ev0
+
+    members = [Tissue(r.tissue) for r in runs]
+    torch.cuda.synchronize()
+    bt = Batch(members)
+    bt.step(dt, 1)
+    bt.sync()
+    tuned = autotune.tune_batch(members, dt, steps=1, max_clones=24) if args.autotune else None
+    if tuned:
+        autotune.apply_batch(bt, tuned)
+    ev1 = sum(int(m.total_events().sum()) for m in members)
+    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a2.record(bt.stream)
+    bt.step(dt, K)
+    b2.record(bt.stream)
+    b2.synchronize()
+    batch_ms = a2.elapsed_time(b2)
+    bt.sync()
+    batch_events = sum(int(m.total_events().sum()) for m in members) - ev1
+    same = all(np.array_equal(x.read_counts(), y.read_counts()) for x, y in zip(plain, members))
+    bt.close()
+    for t in plain + members:
+        t.close()
+    return {"workload": "256 uneven tissues (side 2..64, n in {8,16,32}, kD U[5,20]), dt 0.1",
+            "cells": cells, "steps": K,
+            "batched_events_per_s": batch_events / (batch_ms / 1e3),
+            "plain_events_per_s": plain_events / (plain_ms / 1e3),
+            "speedup": (batch_events / batch_ms) / (plain_events / plain_ms),
+            "batched_cell_steps_per_s": cells * K / (batch_ms / 1e3),
+            "batched_ms_per_step": batch_ms / K, "plain_ms_per_step": plain_ms / K,
+            "bit_identical": bool(same),
+            "tuned": None if not tuned else {
+                "classes": {str(k): list(v) for k, v in tuned["classes"].items()},
+                "steps_per_graph": tuned["steps_per_graph"]}}
+
+
+def serving_leg(args) -> dict:
+    """The first --serving requests of the serving workload (Poisson arrivals
+    at 50 req/s, 1..64 replicas, lognormal sides, 16x16 voxels, T = 20),
+    admitted by a device-memory budget and served by continuous batching;
+    against the plain alternative of serving them one tissue at a time."""
+    import torch
+
+    from paper_1806_10889_gb300.serving import Server, latency_summary
+    from paper_1806_10889_gb300.tissue import Tissue
+
+    reqs = W.serving()[: args.serving]
+    free, _ = torch.cuda.mem_get_info()
+    srv = Server(budget_bytes=int(free * 0.6), chunk_steps=10)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    out = {"requests": len(reqs), "arrivals_per_s": 50.0, "budget_bytes": srv.budget,
+           "served_events_per_s": srv.device_events / wall, "wall_s": wall,
+           "latency": latency_summary(res)}
+    if args.serving_plain:
+        ev, t1 = 0, time.perf_counter()
+        for q in reqs:
+            for spec in q.replica_specs():
+                t = Tissue(spec)
+                t.step(q.dt, q.n_steps)
+                ev += int(t.total_events().sum())
+                t.close()
+        torch.cuda.synchronize()
+        out["plain_events_per_s"] = ev / (time.perf_counter() - t1)
+        out["served_vs_plain"] = out["served_events_per_s"] / out["plain_events_per_s"]
+    return out
 
 
 def _oracle_patch(side: int):
@@ -336,6 +437,11 @@ def main():
     ap.add_argument("--side", type=int, default=0, help="profiling only: tissue side in cells")
     ap.add_argument("--n", type=int, default=0, help="profiling only: voxels per cell side")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain leg")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--serving", type=int, default=0, help="serve the first K requests")
+    ap.add_argument("--serving-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -1,0 +1,177 @@
+"""Serving: ensemble simulation requests admitted by device-memory budget and
+advanced together by continuous batching.
+
+A request asks for ``replicas`` tissues of ``side x side`` cells (n x n
+voxels each) run for ``n_steps`` splitting steps of length dt.  Replica r of
+request q is the tissue (seed = q, tissue_id = r), so its trajectory is
+fixed by the request alone: the same whether it runs alone or among others,
+in whichever slot and batch it lands.
+
+The server loop:
+  1. admit arrived requests in arrival order while the bytes they need
+     (state + library scratch of every replica) fit the budget;
+  2. rebuild the batch when its membership changed;
+  3. advance every active tissue by one chunk of steps with one batch step
+     (one persistent launch per cell-size class and step);
+  4. retire requests whose tissues reached their step count: read the
+     result back, free the memory, record the latency.
+Requests that arrive while others run join at the next chunk boundary, so
+their work overlaps on the device with the work already in flight.
+"""
+from __future__ import annotations
+
+import hashlib
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .batching import Batch
+from .tissue import Tissue, scratch_bytes, state_bytes
+from .workloads import Request
+
+
+@dataclass
+class Result:
+    index: int
+    arrival_s: float
+    admitted_s: float = float("nan")
+    done_s: float = float("nan")
+    events: int = 0
+    cells: int = 0
+    digest: str = ""
+    counts: list = field(default_factory=list)
+    rejected: bool = False
+
+    @property
+    def latency_s(self) -> float:
+        return self.done_s - self.arrival_s
+
+
+@dataclass
+class _Active:
+    req: Request
+    result: Result
+    tissues: list
+    steps_done: int = 0
+    nbytes: int = 0
+
+
+def request_bytes(req: Request) -> int:
+    """Device bytes one request holds while active (all replicas)."""
+    spec = req.replica_specs()[0]
+    return req.replicas * (state_bytes(spec) + scratch_bytes(spec))
+
+
+class Server:
+    """Continuous-batching server over one device.
+
+    budget_bytes: device memory the server may hold for tissue state and
+    scratch; chunk_steps: steps per batch call between admission points;
+    tuned: optional autotuner result (``autotune.tune_batch``) applied to
+    every batch; keep_counts: return each replica's final counts.
+    """
+
+    def __init__(self, budget_bytes: int, chunk_steps: int = 10, tuned: dict | None = None,
+                 keep_counts: bool = False, clock=time.perf_counter):
+        self.budget = int(budget_bytes)
+        self.chunk = int(chunk_steps)
+        self.tuned = tuned
+        self.keep_counts = keep_counts
+        self.clock = clock
+        self.used = 0
+        self.peak_used = 0
+        self.device_events = 0
+
+    def run(self, requests: list[Request], time_scale: float = 1.0) -> list[Result]:
+        import torch
+        if len({r.dt for r in requests}) > 1:
+            raise ValueError("one server run serves requests of a single dt")
+        pending = sorted(requests, key=lambda r: r.arrival_s)
+        results = {r.index: Result(r.index, r.arrival_s * time_scale) for r in pending}
+        active: list[_Active] = []
+        batch = None
+        members_key = None
+        t0 = self.clock()
+        while pending or active:
+            now = self.clock() - t0
+            # 1. admission, arrival order
+            while pending and pending[0].arrival_s * time_scale <= now:
+                req = pending[0]
+                need = request_bytes(req)
+                if need > self.budget:
+                    results[req.index].rejected = True
+                    pending.pop(0)
+                    continue
+                if self.used + need > self.budget:
+                    break
+                pending.pop(0)
+                tissues = [Tissue(s) for s in req.replica_specs()]
+                res = results[req.index]
+                res.admitted_s = now
+                res.cells = sum(s.cells for s in req.replica_specs())
+                active.append(_Active(req, res, tissues, 0, need))
+                self.used += need
+            if not active:
+                if pending:
+                    wait = pending[0].arrival_s * time_scale - (self.clock() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.05))
+                continue
+            # 2. the batch follows the active set
+            key = tuple(id(t) for a in active for t in a.tissues)
+            if key != members_key:
+                if batch is not None:
+                    batch.close()
+                batch = Batch([t for a in active for t in a.tissues])
+                if self.tuned:
+                    from .autotune import apply_batch
+                    apply_batch(batch, self.tuned)
+                members_key = key
+            # 3. one chunk, bounded by the request that finishes first
+            dt = active[0].req.dt
+            k = min(self.chunk, min(a.req.n_steps - a.steps_done for a in active))
+            batch.step(dt, k)
+            batch.sync()
+            for a in active:
+                a.steps_done += k
+            self.peak_used = max(self.peak_used, self.used)
+            # 4. retire finished requests
+            now = self.clock() - t0
+            still = []
+            for a in active:
+                if a.steps_done < a.req.n_steps:
+                    still.append(a)
+                    continue
+                h = hashlib.sha256()
+                ev = 0
+                for t in a.tissues:
+                    c = t.read_counts()
+                    h.update(c.tobytes())
+                    ev += int(t.total_events().sum())
+                    if self.keep_counts:
+                        a.result.counts.append(c)
+                a.result.digest = h.hexdigest()
+                a.result.events = ev
+                a.result.done_s = now
+                self.device_events += ev
+                if batch is not None:
+                    batch.close()
+                    batch, members_key = None, None
+                for t in a.tissues:
+                    t.close()
+                self.used -= a.nbytes
+            active = still
+        if batch is not None:
+            batch.close()
+        torch.cuda.synchronize()
+        return [results[r.index] for r in sorted(requests, key=lambda r: r.index)]
+
+
+def latency_summary(results: list[Result]) -> dict:
+    lat = np.array([r.latency_s for r in results if not r.rejected])
+    if lat.size == 0:
+        return {"p50_s": None, "p99_s": None, "served": 0}
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "served": int(lat.size),
+            "rejected": int(sum(r.rejected for r in results))}

@@ -1,0 +1,50 @@
+"""Serving: continuous batching under a device-memory budget.  Each request's
+result is the same alone and in the mix, bit for bit; the budget is never
+exceeded; a request larger than the budget is refused."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_10889_gb300.workloads import Request
+from tests._util import orc_desc, orc_model
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1806_10889_gb300.serving import Server, latency_summary, request_bytes  # noqa: E402
+
+# staggered arrivals (seconds) so later requests join batches already running
+REQS = [Request(0, 0.00, 3, 4, 16, 7, 0.1), Request(1, 0.02, 2, 6, 8, 5, 0.1),
+        Request(2, 0.04, 4, 3, 16, 9, 0.1), Request(3, 0.05, 1, 5, 32, 4, 0.1),
+        Request(4, 0.05, 2, 2, 10, 6, 0.1)]
+
+
+def test_results_same_alone_and_in_the_mix():
+    mix = Server(budget_bytes=1 << 34, chunk_steps=2, keep_counts=True).run(REQS)
+    assert all(r.digest for r in mix)
+    for req in REQS:
+        alone = Server(budget_bytes=1 << 34, chunk_steps=3).run([req])[0]
+        assert alone.digest == mix[req.index].digest, req.index
+    # and the mix agrees with the oracle for one replica of each request
+    for req, res in zip(REQS, mix):
+        spec = req.replica_specs()[-1]
+        ref = O.init_counts(orc_desc(spec))
+        O.step(orc_desc(spec), orc_model(spec), ref, 0, req.n_steps, req.dt)
+        assert np.array_equal(res.counts[-1], ref), req.index
+    s = latency_summary(mix)
+    assert s["served"] == len(REQS) and s["p99_s"] >= s["p50_s"] > 0
+
+
+def test_budget_admission_and_rejection():
+    one = max(request_bytes(r) for r in REQS)
+    srv = Server(budget_bytes=one, chunk_steps=2)
+    res = srv.run(REQS)
+    assert srv.peak_used <= one
+    assert all(r.digest and not r.rejected for r in res)
+    big = Request(9, 0.0, 64, 40, 16, 2, 0.1)
+    srv2 = Server(budget_bytes=request_bytes(big) - 1, chunk_steps=2)
+    out = srv2.run([big])
+    assert out[0].rejected and latency_summary(out)["served"] == 0

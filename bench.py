@@ -45,9 +45,12 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # Issue-slot peak of the chip: 152 SMs x 4 schedulers x 1 warp-instruction per
 # clock at the 2070 MHz maximum SM clock.
 ISSUE_PEAK_GINST = 152 * 4 * 2.070
-# Warp instructions the chi kernel executes per chi event on this workload,
-# from ncu (smsp__inst_executed.sum / events; profiles/chi_medium_ncu.md).
-CHI_INST_PER_EVENT = None
+# Warp instructions the chi kernel executes per chi event on the medium
+# tissue, per launch variant, from ncu (smsp__inst_executed.sum over the 10
+# timed chi launches / their chi events; profiles/k_chi_medium_metrics.md).
+CHI_INST_PER_EVENT = {("persistent", 16): 325.8}
+# DRAM bytes (read + write) per chi launch from the same capture, per variant.
+CHI_TRAFFIC = {("persistent", 16): 1.312e7}
 # Algorithmic DRAM bytes of one chi launch per cell: the state read + write.
 STATE_BYTES_PER_CELL_RW = lambda V: 2 * 3 * V * 4  # noqa: E731
 
@@ -112,6 +115,19 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def job_totals(dist, local_ms: float, local_events: float, device="cuda"):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of
+    all ranks' events (every rank runs its own replica; weak scaling)."""
+    if dist is None:
+        return local_ms, local_events
+    import torch
+    t = torch.tensor([local_ms, local_events], dtype=torch.float64, device=device)
+    mx, sm = t.clone(), t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
 
 
 def _peaks():
@@ -180,15 +196,7 @@ def run_ours(args, rank, world, local_rank):
     events = int((ev1 - ev0).sum())
     chi_events = int(ev1[0] - ev0[0])
     total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms, float(events)], device="cuda", dtype=torch.float64)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_ms_job, events_job = float(mx[0]), float(sm[1])
-    else:
-        total_ms_job, events_job = total_ms, float(events)
+    total_ms_job, events_job = job_totals(dist, total_ms, float(events))
     value = events_job / (total_ms_job / 1e3)
     cell_steps = spec.cells * args.steps * world
 
@@ -210,13 +218,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         e_ev = float((g.total_events() - e0).sum())
-        if dist:
-            t = torch.tensor([e2e_s, e_ev], device="cuda", dtype=torch.float64)
-            mx = t.clone()
-            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-            sm = t.clone()
-            dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-            e2e_s, e_ev = float(mx[0]), float(sm[1])
+        e2e_s, e_ev = job_totals(dist, e2e_s, e_ev)
         nbytes = spec.state_ints * 4
         e2e = {"value": e_ev / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes}
@@ -225,12 +227,15 @@ def run_ours(args, rank, world, local_rank):
     chi_s = chi_ms / 1e3
     chi_rate = chi_events / chi_s if chi_s > 0 else 0.0
     hbm_achieved = STATE_BYTES_PER_CELL_RW(spec.V) * spec.cells * args.steps / chi_s / 1e9
-    if CHI_INST_PER_EVENT:
-        ach = chi_rate * CHI_INST_PER_EVENT / 1e9
+    variant = (["warp", "persistent"][launch[0]], launch[1])
+    ipe = CHI_INST_PER_EVENT.get(variant) if not (args.side or args.n) else None
+    if ipe:
+        ach = chi_rate * ipe / 1e9
         roofline = {"bound": "alu", "achieved": ach, "peak": ISSUE_PEAK_GINST,
                     "unit": "Gwarp-inst/s", "frac": ach / ISSUE_PEAK_GINST,
-                    "traffic": args.chi_traffic,
-                    "kernel": "k_chi", "inst_per_event": CHI_INST_PER_EVENT,
+                    "traffic": args.chi_traffic or CHI_TRAFFIC.get(variant),
+                    "kernel": f"k_chi ({variant[0]}, {variant[1]} lanes per cell)",
+                    "inst_per_event": ipe,
                     "hbm_gbs": hbm_achieved, "hbm_frac": hbm_achieved / peaks["hbm_gbs"],
                     "peak_source": "152 SMs x 4 issue/clk x 2.070 GHz"}
     else:
@@ -254,6 +259,7 @@ def run_ours(args, rank, world, local_rank):
                                   "lanes_per_cell": launch[1], "warps_per_block": launch[2]}},
         "cell_steps_per_s": cell_steps / (total_ms_job / 1e3),
         "events_per_step": events_job / args.steps,
+        "chi_events_per_step": chi_events / args.steps,
         "chi_ms_per_step": chi_ms / args.steps, "sig_ms_per_step": sig_ms / args.steps,
         "e2e": e2e,
         "gpu_launches": 4 * args.steps,

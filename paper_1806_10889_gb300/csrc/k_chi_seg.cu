@@ -103,8 +103,9 @@ __global__ void __launch_bounds__(256) k_chi_seg(const TissueView* __restrict__ 
   bool have = false, done = false;
   Seg s{0, 2, 1, 0, 1};
   uint32_t cell = 0, step = 0, word3 = 0, key0 = 0, key1 = 0, e = 0, e0 = 0;
-  uint64_t A = 0, P = 0, Em = 0, Rb = 0;
-  int Ek = -1, err = 0;
+  uint64_t A = 0, P = 0, Em = 0, Rb = 0, Em2 = 0, Rb2 = 0;
+  int Ek = -1, Ek2 = -1, err = 0;
+  bool next_ok = false;  // the draws of events e0+H+sl are in Em2/Ek2/Rb2
   double tnow = 0.0;
   int32_t* g = nullptr;
 
@@ -166,6 +167,7 @@ __global__ void __launch_bounds__(256) k_chi_seg(const TissueView* __restrict__ 
         e = 0;
         e0 = 0;
         draw_event(e0 + sl, step, cell, word3, key0, key1, Em, Ek, Rb);
+        next_ok = false;
         err = __any_sync(segmask, ovf) ? kErrOverflow : 0;
         have = true;
         __syncwarp(segmask);
@@ -176,10 +178,42 @@ __global__ void __launch_bounds__(256) k_chi_seg(const TissueView* __restrict__ 
     // ---- one event of every active segment (the whole warp in step) -------
     const bool act = have;
     int j = static_cast<int>(e - e0);
+    // Draws come in batches of H events per segment.  A segment that has used
+    // its batch takes the prepared next one if it has it; when some segment
+    // has none, every segment without a prepared batch draws in the same
+    // pass, so the segments of a warp share the Philox / -ln work.
+    bool must = false;
     if (act && j == H) {
-      e0 += H;
-      j = 0;
-      draw_event(e0 + sl, step, cell, word3, key0, key1, Em, Ek, Rb);
+      if (next_ok) {
+        Em = Em2;
+        Ek = Ek2;
+        Rb = Rb2;
+        next_ok = false;
+        e0 += H;
+        j = 0;
+      } else {
+        must = true;
+      }
+    }
+    if (__any_sync(kFull, must)) {
+      if (must || (act && !next_ok)) {
+        const uint32_t base = e0 + H;  // the batch after the one in use
+        uint64_t m_, r_;
+        int k_;
+        draw_event(base + sl, step, cell, word3, key0, key1, m_, k_, r_);
+        if (must) {
+          Em = m_;
+          Ek = k_;
+          Rb = r_;
+          e0 += H;
+          j = 0;
+        } else {
+          Em2 = m_;
+          Ek2 = k_;
+          Rb2 = r_;
+          next_ok = true;
+        }
+      }
     }
     const uint64_t mE = __shfl_sync(kFull, Em, j, H);
     const int kE = __shfl_sync(kFull, Ek, j, H);

@@ -196,10 +196,9 @@ __device__ __forceinline__ double tau_from(const F53 eq, bool e_zero, uint64_t A
     const uint64_t y = recip115(d);
     const uint64_t plo = mE * y, phi = __umul64hi(mE, y);
     q = sh == 52 ? ((phi << 1) | (plo >> 63)) : ((phi << 2) | (plo >> 62));
-    r = static_cast<int64_t>((mE << sh) - q * d);  // exact: |r| < 2^54
+    // |y - 2^115/d| <= 2 makes the estimate off by at most one either way
+    r = static_cast<int64_t>((mE << sh) - q * d);  // exact: |r| < 2^55
     if (r < 0) { q -= 1; r += static_cast<int64_t>(d); }
-    if (r < 0) { q -= 1; r += static_cast<int64_t>(d); }
-    if (r >= static_cast<int64_t>(d)) { q += 1; r -= static_cast<int64_t>(d); }
     if (r >= static_cast<int64_t>(d)) { q += 1; r -= static_cast<int64_t>(d); }
   }
   const uint64_t twice = static_cast<uint64_t>(r) << 1;

@@ -48,9 +48,9 @@ ISSUE_PEAK_GINST = 152 * 4 * 2.070
 # Warp instructions the chi kernel executes per chi event on the medium
 # tissue, per launch variant, from ncu (smsp__inst_executed.sum over the 10
 # timed chi launches / their chi events; profiles/k_chi_medium_metrics.md).
-CHI_INST_PER_EVENT = {("persistent", 16): 325.8}
+CHI_INST_PER_EVENT = {("persistent", 16, 0): 325.8}
 # DRAM bytes (read + write) per chi launch from the same capture, per variant.
-CHI_TRAFFIC = {("persistent", 16): 1.312e7}
+CHI_TRAFFIC = {("persistent", 16, 0): 1.312e7}
 # Algorithmic DRAM bytes of one chi launch per cell: the state read + write.
 STATE_BYTES_PER_CELL_RW = lambda V: 2 * 3 * V * 4  # noqa: E731
 
@@ -158,7 +158,7 @@ def run_ours(args, rank, world, local_rank):
         spec = replace(spec, tissue_id=rank)
     g = Tissue(spec)
     if args.kernel == "persistent":
-        g.set_launch_config(1, args.lanes, args.chi_wpb or 4, 0)
+        g.set_launch_config(1, args.lanes, args.chi_wpb or 4, 0, args.layout)
     elif args.kernel == "warp":
         g.set_launch(args.chi_wpb or DEFAULT_CHI_WPB)
     launch = g.launch_config()
@@ -227,7 +227,7 @@ def run_ours(args, rank, world, local_rank):
     chi_s = chi_ms / 1e3
     chi_rate = chi_events / chi_s if chi_s > 0 else 0.0
     hbm_achieved = STATE_BYTES_PER_CELL_RW(spec.V) * spec.cells * args.steps / chi_s / 1e9
-    variant = (["warp", "persistent"][launch[0]], launch[1])
+    variant = (["warp", "persistent"][launch[0]], launch[1], launch[4])
     ipe = CHI_INST_PER_EVENT.get(variant) if not (args.side or args.n) else None
     if ipe:
         ach = chi_rate * ipe / 1e9
@@ -256,7 +256,8 @@ def run_ours(args, rank, world, local_rank):
                    "voxels_per_cell": spec.V, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}",
                    "chi_launch": {"kernel": ["warp", "persistent"][launch[0]],
-                                  "lanes_per_cell": launch[1], "warps_per_block": launch[2]}},
+                                  "lanes_per_cell": launch[1], "warps_per_block": launch[2],
+                                  "smem_layout": ["prefix", "recompute"][launch[4]]}},
         "cell_steps_per_s": cell_steps / (total_ms_job / 1e3),
         "events_per_step": events_job / args.steps,
         "chi_events_per_step": chi_events / args.steps,
@@ -437,6 +438,8 @@ def main():
     ap.add_argument("--chi-wpb", type=int, default=0)
     ap.add_argument("--kernel", choices=["default", "warp", "persistent"], default="default")
     ap.add_argument("--lanes", type=int, choices=[16, 32], default=16)
+    ap.add_argument("--layout", type=int, choices=[0, 1], default=0,
+                    help="persistent kernel: 0 prefix arrays, 1 recompute")
     ap.add_argument("--chi-traffic", type=float, default=None,
                     help="DRAM bytes per chi launch from an ncu capture, if known")
     ap.add_argument("--ref-side", type=int, default=16)

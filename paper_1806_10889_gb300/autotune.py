@@ -16,7 +16,7 @@ import threading
 
 import numpy as np
 
-from .tissue import KERNEL_PERSISTENT, KERNEL_WARP, Tissue
+from .tissue import KERNEL_PERSISTENT, KERNEL_WARP, LAYOUT_PREFIX, LAYOUT_RECOMPUTE, Tissue
 from .workloads import TissueSpec
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
@@ -28,19 +28,21 @@ class VariantMismatch(RuntimeError):
 
 
 def tissue_candidates(V: int) -> list[tuple]:
-    """(kernel, lanes per cell, warps per block, blocks) candidates for cells of V voxels."""
-    c = [(KERNEL_WARP, 32, w, 0) for w in (2, 4, 8)]
-    c += [(KERNEL_PERSISTENT, 32, w, 0) for w in (2, 4)]
-    if V <= 256:
-        c += [(KERNEL_PERSISTENT, 16, w, 0) for w in (2, 4, 8)]
+    """(kernel, lanes per cell, warps per block, blocks, shared-memory layout)
+    candidates for cells of V voxels."""
+    c = [(KERNEL_WARP, 32, w, 0, LAYOUT_PREFIX) for w in (2, 4, 8)]
+    for lanes in ((16, 32) if V <= 256 else (32,)):
+        c += [(KERNEL_PERSISTENT, lanes, w, 0, LAYOUT_PREFIX) for w in (2, 4)]
+        c += [(KERNEL_PERSISTENT, lanes, w, 0, LAYOUT_RECOMPUTE) for w in (2, 4)]
     return c
 
 
 def batch_class_candidates(V: int) -> list[tuple]:
-    """(lanes per cell, warps per block) candidates for one cell-size class."""
-    c = [(32, w) for w in (2, 4)]
-    if V <= 256:
-        c += [(16, w) for w in (2, 4, 8)]
+    """(lanes per cell, warps per block, layout) candidates for one cell-size class."""
+    c = []
+    for lanes in ((16, 32) if V <= 256 else (32,)):
+        c += [(lanes, w, LAYOUT_PREFIX) for w in (2, 4)]
+        c += [(lanes, w, LAYOUT_RECOMPUTE) for w in (2, 4)]
     return c
 
 
@@ -72,9 +74,10 @@ def _size_class(cells: int) -> int:
     return int(2 ** round(math.log2(max(cells, 1))))
 
 
-def _time_steps(run, n_steps: int) -> float:
+def _time_steps(run, n_steps: int, stream=None) -> float:
+    """Device milliseconds of run(n_steps), timed on the stream it uses."""
     import torch
-    stream = torch.cuda.current_stream()
+    stream = stream if stream is not None else torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     run(n_steps)
@@ -87,7 +90,7 @@ def tune_tissue(spec: TissueSpec, dt: float, state: np.ndarray | None = None,
                 step_index: int = 0, steps: int = 2, candidates: list[tuple] | None = None,
                 use_cache: bool = True) -> dict:
     """Pick the fastest chi launch for this tissue; returns
-    {"config": (kernel, lanes, warps, blocks), "ms": {str(config): ms}}."""
+    {"config": (kernel, lanes, warps, blocks, layout), "ms": {str(config): ms}}."""
     key = f"tissue|{_gpu_name()}|V={spec.V}|cells~{_size_class(spec.cells)}|dt={dt}"
     if use_cache and candidates is None:
         hit = _load().get(key)
@@ -119,12 +122,12 @@ def tune_tissue(spec: TissueSpec, dt: float, state: np.ndarray | None = None,
 
 def tune_batch(members: list[Tissue], dt: float, steps: int = 1, max_clones: int = 48,
                schedules=(1, 4), use_cache: bool = True) -> dict:
-    """Pick (lanes per cell, warps per block) per cell-size class and the
+    """Pick (lanes per cell, warps per block, layout) per cell-size class and the
     steps-per-graph schedule for a batch of these tissues.
 
     Each class is tuned on clones of up to ``max_clones`` of its members
     (their current state and step index), so the members themselves do not
-    move.  Returns {"classes": {V: (lanes, warps)}, "steps_per_graph": k}.
+    move.  Returns {"classes": {V: (lanes, warps, layout)}, "steps_per_graph": k}.
     """
     from .batching import Batch
 
@@ -151,36 +154,37 @@ def tune_batch(members: list[Tissue], dt: float, steps: int = 1, max_clones: int
     chosen, timings = {}, {}
     for V, ms in sorted(by_v.items()):
         ref = None
-        for lanes, wpb in batch_class_candidates(V):
+        for lanes, wpb, layout in batch_class_candidates(V):
             clones = clones_of(ms)
             b = Batch(clones)
-            b.set_class_launch(V, lanes, wpb)
+            b.set_class_launch(V, lanes, wpb, layout)
             b.step(dt, 1)
             b.sync()
-            ms_ = _time_steps(lambda n: b.step(dt, n), steps)
+            ms_ = _time_steps(lambda n: b.step(dt, n), steps, b.stream)
             b.sync()
-            timings[f"{V}:{lanes}x{wpb}"] = ms_
+            timings[f"{V}:{lanes}x{wpb}/{layout}"] = ms_
             out = [c.read_counts() for c in clones]
             if ref is None:
                 ref = out
             elif not all(np.array_equal(x, y) for x, y in zip(out, ref)):
-                raise VariantMismatch(f"batch launch {lanes}x{wpb} changed results (V={V})")
+                raise VariantMismatch(f"batch launch {lanes}x{wpb}/{layout} changed results (V={V})")
             b.close()
             for c in clones:
                 c.close()
-        chosen[V] = min(batch_class_candidates(V), key=lambda c: timings[f"{V}:{c[0]}x{c[1]}"])
+        chosen[V] = min(batch_class_candidates(V),
+                        key=lambda c: timings[f"{V}:{c[0]}x{c[1]}/{c[2]}"])
     # schedule: tune on a clone of the whole (bounded) batch with the chosen classes
     best_k, best_ms = 1, None
     for k in schedules:
         clones = clones_of([m for ms in by_v.values() for m in ms][:max_clones])
         b = Batch(clones)
-        for V, (lanes, wpb) in chosen.items():
+        for V, (lanes, wpb, layout) in chosen.items():
             if any(c.spec.V == V for c in clones):
-                b.set_class_launch(V, lanes, wpb)
+                b.set_class_launch(V, lanes, wpb, layout)
         b.set_schedule(k)
         b.step(dt, k)
         b.sync()
-        ms_ = _time_steps(lambda n: b.step(dt, n), k * max(1, steps))
+        ms_ = _time_steps(lambda n: b.step(dt, n), k * max(1, steps), b.stream)
         timings[f"steps_per_graph={k}"] = ms_
         if best_ms is None or ms_ < best_ms:
             best_k, best_ms = k, ms_
@@ -193,9 +197,10 @@ def tune_batch(members: list[Tissue], dt: float, steps: int = 1, max_clones: int
 
 
 def apply_batch(batch, tuned: dict) -> None:
-    for V, (lanes, wpb) in tuned["classes"].items():
+    from .tissue import TissueError
+    for V, cfg in tuned["classes"].items():
         try:
-            batch.set_class_launch(V, lanes, wpb)
-        except Exception:
+            batch.set_class_launch(V, *cfg)
+        except TissueError:
             pass  # the class is not present in this batch
     batch.set_schedule(tuned["steps_per_graph"])

@@ -25,8 +25,10 @@ class Batch:
         _check(lib().tissue_batch_create(arr, len(members), C.c_void_p(self.stream.cuda_stream),
                                          C.byref(self._h)), "tissue_batch_create")
 
-    def set_class_launch(self, V: int, lanes_per_cell: int, warps_per_block: int):
-        _check(lib().tissue_batch_set_class_launch(self._h, V, lanes_per_cell, warps_per_block),
+    def set_class_launch(self, V: int, lanes_per_cell: int, warps_per_block: int,
+                         smem_layout: int = 0):
+        _check(lib().tissue_batch_set_class_launch(self._h, V, lanes_per_cell, warps_per_block,
+                                                   smem_layout),
                "tissue_batch_set_class_launch")
 
     def set_schedule(self, steps_per_graph: int):

@@ -26,7 +26,7 @@ namespace {
 
 struct ClassPlan {
   uint32_t V;
-  uint32_t lanes, warps_per_block;
+  uint32_t lanes, warps_per_block, layout;
   size_t items_off;  // offset (in uint2) into the item buffer
   uint32_t n_items;
 };
@@ -57,7 +57,7 @@ int enqueue_step(tissue_batch* b, double dt) {
       return TISSUE_E_CUDA;
     if (launch_chi_seg(b->d_views, b->d_items + p.items_off, p.n_items, b->d_counters + c, p.V,
                        static_cast<int>(p.lanes), static_cast<int>(p.warps_per_block), 0, 0u, dt,
-                       b->stream) != cudaSuccess)
+                       p.layout == TISSUE_LAYOUT_PREFIX, b->stream) != cudaSuccess)
       return TISSUE_E_CUDA;
   }
   if (launch_sig_list(b->d_views, b->d_items + b->xface_off, b->n_xfaces, 0, dt, b->stream) !=
@@ -116,6 +116,7 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
     p.V = kv.first;
     p.lanes = kv.first <= 256 ? 16u : 32u;
     p.warps_per_block = 4;
+    p.layout = TISSUE_LAYOUT_PREFIX;
     p.items_off = items.size();
     p.n_items = static_cast<uint32_t>(kv.second.size());
     items.insert(items.end(), kv.second.begin(), kv.second.end());
@@ -162,18 +163,22 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
 }
 
 int tissue_batch_set_class_launch(tissue_batch* b, uint32_t V, uint32_t lanes_per_cell,
-                                  uint32_t warps_per_block) {
+                                  uint32_t warps_per_block, uint32_t smem_layout) {
   if (!b) return TISSUE_E_ARG;
   if (lanes_per_cell != 16 && lanes_per_cell != 32) return TISSUE_E_ARG;
   if (lanes_per_cell == 16 && V > 256) return TISSUE_E_ARG;
-  if (warps_per_block < 1 || warps_per_block > 8) return TISSUE_E_ARG;
+  if (smem_layout != TISSUE_LAYOUT_PREFIX && smem_layout != TISSUE_LAYOUT_RECOMPUTE)
+    return TISSUE_E_ARG;
+  const bool pre = smem_layout == TISSUE_LAYOUT_PREFIX;
+  if (warps_per_block < 1 || warps_per_block > (pre ? 8u : 4u)) return TISSUE_E_ARG;
   if (static_cast<size_t>(warps_per_block) * (32 / lanes_per_cell) *
-          seg_bytes_for(V, static_cast<int>(lanes_per_cell)) > 227 * 1024)
+          seg_bytes_for(V, static_cast<int>(lanes_per_cell), pre) > 227 * 1024)
     return TISSUE_E_ARG;
   for (ClassPlan& p : b->classes)
     if (p.V == V) {
       p.lanes = lanes_per_cell;
       p.warps_per_block = warps_per_block;
+      p.layout = smem_layout;
       drop_graph(b);
       return TISSUE_OK;
     }

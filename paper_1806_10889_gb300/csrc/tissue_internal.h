@@ -52,10 +52,13 @@ cudaError_t launch_chi(const TissueView& t, uint32_t step_off, double dt, int wa
 // of d_views[0] in order.  H = 16 or 32 lanes per cell; vmax_cells is the
 // largest V among the listed tissues (sizes shared memory).  blocks <= 0
 // picks a grid that fills every SM.
+// pre: keep the per-voxel prefix array (layout 0) or recompute the selected
+// block (layout 1, at most 4 warps per block).
 cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
                            uint32_t* d_counter, uint32_t vmax_cells, int H, int warps_per_block,
-                           int blocks, uint32_t step_off, double dt, cudaStream_t stream);
-uint32_t seg_bytes_for(uint32_t V, int H);
+                           int blocks, uint32_t step_off, double dt, bool pre,
+                           cudaStream_t stream);
+uint32_t seg_bytes_for(uint32_t V, int H, bool pre);
 cudaError_t launch_sig_list(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
                             int axis, double dt, cudaStream_t stream);
 cudaError_t launch_advance_list(const TissueView* d_views, uint32_t n, cudaStream_t stream);

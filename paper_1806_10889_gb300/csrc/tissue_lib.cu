@@ -32,7 +32,7 @@ struct tissue {
   uint32_t* d_step = nullptr;
   int* d_err = nullptr;
   uint32_t step_index = 0;
-  tissue_launch cfg{TISSUE_KERNEL_WARP, 32, 4, 0};
+  tissue_launch cfg{TISSUE_KERNEL_WARP, 32, 4, 0, TISSUE_LAYOUT_PREFIX};
   TissueView* d_view = nullptr;   // device copy of the view, for the persistent kernel
   uint32_t* d_work = nullptr;     // work-list counter of the persistent kernel
 };
@@ -107,7 +107,8 @@ cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt
     if (e != cudaSuccess) return e;
     return launch_chi_seg(t->d_view, nullptr, t->d.width * t->d.height, t->d_work, v.V,
                           static_cast<int>(c.lanes_per_cell), static_cast<int>(c.warps_per_block),
-                          static_cast<int>(c.blocks), i, dt, t->stream);
+                          static_cast<int>(c.blocks), i, dt,
+                          c.smem_layout == TISSUE_LAYOUT_PREFIX, t->stream);
   }
   return launch_chi(v, i, dt, static_cast<int>(c.warps_per_block), t->stream);
 }
@@ -195,7 +196,8 @@ int tissue_create(const tissue_desc* d, void* dev_counts, size_t bytes, void* cu
   t->stream = static_cast<cudaStream_t>(cuda_stream);
   // Default chi launch: two cells per warp on the persistent kernel where a
   // cell fits 16 lanes (V <= 256), otherwise one warp per cell.
-  if (d->n * d->n <= 256) t->cfg = tissue_launch{TISSUE_KERNEL_PERSISTENT, 16, 4, 0};
+  if (d->n * d->n <= 256)
+    t->cfg = tissue_launch{TISSUE_KERNEL_PERSISTENT, 16, 4, 0, TISSUE_LAYOUT_PREFIX};
   const ScratchLayout L = layout(d);
   if (cudaMalloc(&t->scratch, L.total) != cudaSuccess) {
     cudaGetLastError();
@@ -370,7 +372,7 @@ int tissue_sync(tissue* t) {
 
 int tissue_set_launch(tissue* t, uint32_t chi_warps_per_block) {
   if (!t || chi_warps_per_block < 1 || chi_warps_per_block > 16) return TISSUE_E_ARG;
-  t->cfg = tissue_launch{TISSUE_KERNEL_WARP, 32, chi_warps_per_block, 0};
+  t->cfg = tissue_launch{TISSUE_KERNEL_WARP, 32, chi_warps_per_block, 0, TISSUE_LAYOUT_PREFIX};
   return TISSUE_OK;
 }
 
@@ -382,9 +384,12 @@ int tissue_set_launch_config(tissue* t, const tissue_launch* c) {
   } else if (c->kernel == TISSUE_KERNEL_PERSISTENT) {
     if (c->lanes_per_cell != 32 && c->lanes_per_cell != 16) return TISSUE_E_ARG;
     if (c->lanes_per_cell == 16 && V > 256) return TISSUE_E_ARG;
-    if (c->warps_per_block < 1 || c->warps_per_block > 8) return TISSUE_E_ARG;
+    if (c->smem_layout != TISSUE_LAYOUT_PREFIX && c->smem_layout != TISSUE_LAYOUT_RECOMPUTE)
+      return TISSUE_E_ARG;
+    const bool pre = c->smem_layout == TISSUE_LAYOUT_PREFIX;
+    if (c->warps_per_block < 1 || c->warps_per_block > (pre ? 8u : 4u)) return TISSUE_E_ARG;
     if (static_cast<size_t>(c->warps_per_block) * (32 / c->lanes_per_cell) *
-            seg_bytes_for(V, static_cast<int>(c->lanes_per_cell)) > 227 * 1024)
+            seg_bytes_for(V, static_cast<int>(c->lanes_per_cell), pre) > 227 * 1024)
       return TISSUE_E_ARG;
   } else {
     return TISSUE_E_ARG;

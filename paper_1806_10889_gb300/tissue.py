@@ -47,11 +47,13 @@ class Model(C.Structure):
 
 
 KERNEL_WARP, KERNEL_PERSISTENT = 0, 1
+LAYOUT_PREFIX, LAYOUT_RECOMPUTE = 0, 1
 
 
 class Launch(C.Structure):
     _fields_ = [("kernel", C.c_uint32), ("lanes_per_cell", C.c_uint32),
-                ("warps_per_block", C.c_uint32), ("blocks", C.c_uint32)]
+                ("warps_per_block", C.c_uint32), ("blocks", C.c_uint32),
+                ("smem_layout", C.c_uint32)]
 
 
 # Every exported symbol of include/tissue.h with (restype, argtypes).
@@ -77,7 +79,8 @@ SIGNATURES = {
                                       C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tissue_selftest_time": (C.c_int, [C.c_uint64, C.c_uint64, _P(C.c_uint64)]),
     "tissue_batch_create": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, _P(C.c_void_p)]),
-    "tissue_batch_set_class_launch": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32]),
+    "tissue_batch_set_class_launch": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32,
+                                                 C.c_uint32]),
     "tissue_batch_step": (C.c_int, [C.c_void_p, C.c_double, C.c_uint32]),
     "tissue_batch_set_schedule": (C.c_int, [C.c_void_p, C.c_uint32]),
     "tissue_batch_sync": (C.c_int, [C.c_void_p]),
@@ -195,14 +198,14 @@ class Tissue:
         _check(lib().tissue_set_launch(self._h, int(chi_warps_per_block)), "tissue_set_launch")
 
     def set_launch_config(self, kernel: int, lanes_per_cell: int = 32, warps_per_block: int = 4,
-                          blocks: int = 0):
-        c = Launch(kernel, lanes_per_cell, warps_per_block, blocks)
+                          blocks: int = 0, smem_layout: int = LAYOUT_PREFIX):
+        c = Launch(kernel, lanes_per_cell, warps_per_block, blocks, smem_layout)
         _check(lib().tissue_set_launch_config(self._h, C.byref(c)), "tissue_set_launch_config")
 
     def launch_config(self) -> tuple:
         c = Launch()
         _check(lib().tissue_get_launch_config(self._h, C.byref(c)), "tissue_get_launch_config")
-        return (c.kernel, c.lanes_per_cell, c.warps_per_block, c.blocks)
+        return (c.kernel, c.lanes_per_cell, c.warps_per_block, c.blocks, c.smem_layout)
 
     def step(self, dt: float, n_steps: int = 1):
         _check(lib().tissue_step(self._h, float(dt), int(n_steps)), "tissue_step")

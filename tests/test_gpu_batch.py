@@ -55,13 +55,14 @@ def test_batch_matches_oracle_per_member(steps_per_graph):
 
 def test_batch_class_launch_shapes_give_the_same_bits():
     results = []
-    for lanes, wpb in ((16, 4), (32, 2), (16, 1), (32, 8)):
+    for lanes, wpb, layout in ((16, 4, 0), (32, 2, 0), (16, 1, 0), (32, 8, 0), (16, 4, 1),
+                               (32, 2, 1)):
         members = [T.Tissue(s) for s in MIX]
         b = Batch(members)
         for V in {s.V for s in MIX}:
             if lanes == 16 and V > 256:
                 continue
-            b.set_class_launch(V, lanes, wpb)
+            b.set_class_launch(V, lanes, wpb, layout)
         b.step(0.2, 4)
         b.sync()
         results.append([m.read_counts() for m in members])
@@ -99,8 +100,8 @@ def test_batch_rejects_bad_input():
         Batch([a, a])
     b = Batch([a])
     with pytest.raises(T.TissueError):
-        b.set_class_launch(64, 16, 99)
+        b.set_class_launch(64, 16, 99, 0)
     with pytest.raises(T.TissueError):
-        b.set_class_launch(1024, 16, 4)  # no such class
+        b.set_class_launch(1024, 16, 4, 0)  # no such class
     b.close()
     a.close()

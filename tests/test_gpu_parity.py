@@ -95,8 +95,13 @@ def test_launch_shape_does_not_change_results(wpb):
     _run_both(spec, 0.1, 2, wpb=wpb, every=False)
 
 
-PERSISTENT = [(T.KERNEL_PERSISTENT, 32, 4, 0), (T.KERNEL_PERSISTENT, 16, 4, 0),
-              (T.KERNEL_PERSISTENT, 16, 2, 1), (T.KERNEL_PERSISTENT, 32, 1, 3)]
+PERSISTENT = [(T.KERNEL_PERSISTENT, 32, 4, 0, T.LAYOUT_PREFIX),
+              (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_PREFIX),
+              (T.KERNEL_PERSISTENT, 16, 2, 1, T.LAYOUT_PREFIX),
+              (T.KERNEL_PERSISTENT, 32, 1, 3, T.LAYOUT_PREFIX),
+              (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE),
+              (T.KERNEL_PERSISTENT, 32, 2, 0, T.LAYOUT_RECOMPUTE),
+              (T.KERNEL_PERSISTENT, 16, 1, 2, T.LAYOUT_RECOMPUTE)]
 
 
 @pytest.mark.parametrize("config", PERSISTENT)
@@ -119,19 +124,23 @@ def test_launch_config_validation():
         g.set_launch_config(T.KERNEL_PERSISTENT, 16, 4, 0)  # V = 1024 needs 32 lanes
     with pytest.raises(T.TissueError):
         g.set_launch_config(7, 32, 4, 0)
+    with pytest.raises(T.TissueError):
+        g.set_launch_config(T.KERNEL_PERSISTENT, 32, 8, 0, T.LAYOUT_RECOMPUTE)  # <= 4 warps
     g.set_launch_config(T.KERNEL_PERSISTENT, 32, 2, 0)
-    assert g.launch_config() == (T.KERNEL_PERSISTENT, 32, 2, 0)
+    assert g.launch_config() == (T.KERNEL_PERSISTENT, 32, 2, 0, T.LAYOUT_PREFIX)
     g.close()
 
 
 @pytest.mark.parametrize("config", [None, (T.KERNEL_PERSISTENT, 16, 4, 0),
-                                    (T.KERNEL_PERSISTENT, 32, 4, 0)])
+                                    (T.KERNEL_PERSISTENT, 32, 4, 0),
+                                    (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE)])
 def test_in_voxel_binding_channels(config):
     spec = TissueSpec(3, 3, 6, seed=17).with_model(k_in=0.02, k_off=0.7)
     _run_both(spec, 0.2, 4, config=config)
 
 
-@pytest.mark.parametrize("config", [None, (T.KERNEL_WARP, 32, 4, 0)])
+@pytest.mark.parametrize("config", [None, (T.KERNEL_WARP, 32, 4, 0),
+                                    (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE)])
 def test_medium_config_full_tissue(config):
     """64x64 cells of 16x16 voxels at dt = 0.1: the whole tissue, two steps,
     in the default launch shape (the benchmark's) and the warp kernel."""
@@ -227,7 +236,8 @@ def test_rerun_is_bit_identical_and_totals_add_up():
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
 
 
-@pytest.mark.parametrize("config", [None, (T.KERNEL_PERSISTENT, 16, 4, 0)])
+@pytest.mark.parametrize("config", [None, (T.KERNEL_PERSISTENT, 16, 4, 0),
+                                    (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE)])
 def test_overflow_is_reported(config):
     spec = TissueSpec(2, 1, 2, seed=1, init_lambda=(0.0, 0.0, 0.0)).with_model(hopD=1000.0)
     g = Tissue(spec)

@@ -148,10 +148,10 @@ int tissue_set_launch(tissue* t, uint32_t chi_warps_per_block);
 #define TISSUE_KERNEL_WARP 0u       /* one warp per cell, one launch over all cells */
 #define TISSUE_KERNEL_PERSISTENT 1u /* persistent kernel, cells taken from a work list */
 #define TISSUE_LAYOUT_PREFIX 0u    /* persistent kernel keeps per-voxel prefix sums (20 B/voxel) */
-#define TISSUE_LAYOUT_RECOMPUTE 1u /* keeps counts only (12 B/voxel); <= 4 warps per block */
+#define TISSUE_LAYOUT_RECOMPUTE 1u /* counts only (12 B/voxel); <= 4 warps per block, V <= lanes^2 */
 typedef struct {
   uint32_t kernel;          /* TISSUE_KERNEL_WARP or TISSUE_KERNEL_PERSISTENT */
-  uint32_t lanes_per_cell;  /* persistent kernel: 32, or 16 (two cells per warp; V <= 256) */
+  uint32_t lanes_per_cell;  /* persistent kernel: 32, or 16 (two cells per warp) */
   uint32_t warps_per_block; /* 1..16 (warp kernel) or 1..8 (persistent kernel) */
   uint32_t blocks;          /* persistent kernel grid; 0 = enough to fill every SM */
   uint32_t smem_layout;     /* persistent kernel: TISSUE_LAYOUT_PREFIX or _RECOMPUTE */
@@ -180,8 +180,8 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
                         tissue_batch** out);
 
 /* Launch shape of the chi launch of the class of cells with V voxels:
- * 16 (V <= 256) or 32 lanes per cell, 1..8 warps per block (1..4 with the
- * recompute layout), shared-memory layout TISSUE_LAYOUT_*.  The default is
+ * 16 or 32 lanes per cell, 1..8 warps per block (1..4 with the recompute
+ * layout, which also needs V <= lanes^2), shared-memory layout TISSUE_LAYOUT_*.  The default is
  * 16 lanes where allowed, 4 warps per block, prefix layout.  Results never
  * depend on it. */
 int tissue_batch_set_class_launch(tissue_batch* b, uint32_t V, uint32_t lanes_per_cell,

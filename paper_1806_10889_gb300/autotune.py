@@ -31,18 +31,20 @@ def tissue_candidates(V: int) -> list[tuple]:
     """(kernel, lanes per cell, warps per block, blocks, shared-memory layout)
     candidates for cells of V voxels."""
     c = [(KERNEL_WARP, 32, w, 0, LAYOUT_PREFIX) for w in (2, 4, 8)]
-    for lanes in ((16, 32) if V <= 256 else (32,)):
-        c += [(KERNEL_PERSISTENT, lanes, w, 0, LAYOUT_PREFIX) for w in (2, 4)]
-        c += [(KERNEL_PERSISTENT, lanes, w, 0, LAYOUT_RECOMPUTE) for w in (2, 4)]
+    for lanes in (16, 32):
+        c += [(KERNEL_PERSISTENT, lanes, w, 0, LAYOUT_PREFIX) for w in (1, 2, 4)]
+        if V <= lanes * lanes:
+            c += [(KERNEL_PERSISTENT, lanes, w, 0, LAYOUT_RECOMPUTE) for w in (2, 4)]
     return c
 
 
 def batch_class_candidates(V: int) -> list[tuple]:
     """(lanes per cell, warps per block, layout) candidates for one cell-size class."""
     c = []
-    for lanes in ((16, 32) if V <= 256 else (32,)):
-        c += [(lanes, w, LAYOUT_PREFIX) for w in (2, 4)]
-        c += [(lanes, w, LAYOUT_RECOMPUTE) for w in (2, 4)]
+    for lanes in (16, 32):
+        c += [(lanes, w, LAYOUT_PREFIX) for w in (1, 2, 4)]
+        if V <= lanes * lanes:
+            c += [(lanes, w, LAYOUT_RECOMPUTE) for w in (2, 4)]
     return c
 
 

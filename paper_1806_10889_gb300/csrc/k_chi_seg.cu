@@ -28,8 +28,9 @@ constexpr int kViewBytes = (static_cast<int>(sizeof(TissueView)) + 15) & ~15;
 static_assert(sizeof(TissueView) % 8 == 0, "view copy uses 8-byte words");
 
 struct Seg {
-  int V, n, B, lb;  // voxels, side, voxels per lane, log2 B
+  int V, n, B, lb;  // voxels, side, voxels per lane block, log2 B
   uint32_t magic;
+  int qb;           // log2 of the voxels each lane covers inside one block (B > H)
 };
 
 // Existence mask of the four neighbour directions (-x, +x, -y, +y) of v.
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
   const ChanLane cl = chan_lane(sl);
 
   bool have = false, done = false;
-  Seg s{0, 2, 1, 0, 1};
+  Seg s{0, 2, 1, 0, 1, 0};
   uint32_t cell = 0, step = 0, word3 = 0, key0 = 0, key1 = 0, e = 0, e0 = 0;
   uint64_t A = 0, P = 0, Em = 0, Rb = 0, Em2 = 0, Rb2 = 0;
   int Ek = -1, Ek2 = -1, err = 0;
@@ -136,6 +137,8 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
         s.lb = 0;
         while ((H << s.lb) < s.V) ++s.lb;
         s.B = 1 << s.lb;
+        s.qb = 0;
+        while ((H << s.qb) < s.B) ++s.qb;
         g = sv->counts + static_cast<size_t>(cell) * 3 * s.V;
         if ((s.V & 3) == 0) {
           const int V4 = s.V >> 2;
@@ -236,7 +239,9 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     const QRates& q = sv->q;
     uint64_t pv = ~0ull;
     if (PRE) {
-      if (sl < s.B && vb + sl < s.V) pv = pre[vb + sl];
+      // lane sl covers voxels vb + sl*Q .. + Q-1 of the block (Q = 2^qb; 1 if B <= H)
+      const int q0 = vb + (sl << s.qb);
+      if ((sl << s.qb) < s.B && q0 < s.V) pv = pre[min(q0 + (1 << s.qb) - 1, s.V - 1)];
     } else {
       // the block's voxel propensities, recomputed, then their running sum
       bool unused = false;
@@ -252,9 +257,29 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     const unsigned m2 = (__ballot_sync(kFull, r1 < pv) >> (seg * H)) & (H == 32 ? kFull : 0xFFFFu);
     const int i2 = m2 ? __ffs(m2) - 1 : 0;
     const uint64_t pp = __shfl_sync(kFull, pv, i2 > 0 ? i2 - 1 : 0, H);
-    const uint64_t r2 = r1 - (i2 > 0 ? pp : 0ull);
-    int v = vb + i2;
-    const bool bad1 = act && Aa != 0ull && (m1 == 0u || m2 == 0u || i2 >= s.B || v >= s.V);
+    uint64_t r2 = r1 - (i2 > 0 ? pp : 0ull);
+    int v = vb + (i2 << s.qb);
+    bool bad_q = false;
+    if (PRE && s.qb > 0) {
+      // the voxel inside lane i2's run of Q voxels: a short uniform scan
+      uint64_t before_v = i2 > 0 ? pp : 0ull;
+      int pick = -1;
+      for (int kq = 0; kq < (1 << s.qb); ++kq) {
+        const int idx = v + kq;
+        if (pick < 0 && idx < s.V) {
+          const uint64_t x = pre[idx];
+          if (r1 < x) {
+            pick = idx;
+            r2 = r1 - before_v;
+          }
+          before_v = x;
+        }
+      }
+      bad_q = pick < 0;
+      v = pick < 0 ? v : pick;
+    }
+    const bool bad1 = act && Aa != 0ull &&
+                      (m1 == 0u || m2 == 0u || (i2 << s.qb) >= s.B || v >= s.V || bad_q);
     if (bad1 || v >= s.V) v = 0;
 
     // channel: closed-form running sums
@@ -353,12 +378,16 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
         P += sl >= bu ? du : 0ull;
         A += du;
       }
-      if (PRE && sl < s.B) {
-        const int iv = (bv << s.lb) + sl;
-        if (sl >= (v & (s.B - 1)) && iv < s.V) pre[iv] += dv;
-        if (u >= 0) {
-          const int iu = ((u >> s.lb) << s.lb) + sl;
-          if (sl >= (u & (s.B - 1)) && iu < s.V) pre[iu] += du;
+      if (PRE && (sl << s.qb) < s.B) {
+        // prefix entries from the changed voxel to the end of its block
+        for (int kq = 0; kq < (1 << s.qb); ++kq) {
+          const int off = (sl << s.qb) + kq;  // position inside the block
+          const int iv = (bv << s.lb) + off;
+          if (off >= (v & (s.B - 1)) && iv < s.V) pre[iv] += dv;
+          if (u >= 0) {
+            const int iu = ((u >> s.lb) << s.lb) + off;
+            if (off >= (u & (s.B - 1)) && iu < s.V) pre[iu] += du;
+          }
         }
       }
       tnow = tn;

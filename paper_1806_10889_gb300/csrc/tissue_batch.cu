@@ -166,8 +166,9 @@ int tissue_batch_set_class_launch(tissue_batch* b, uint32_t V, uint32_t lanes_pe
                                   uint32_t warps_per_block, uint32_t smem_layout) {
   if (!b) return TISSUE_E_ARG;
   if (lanes_per_cell != 16 && lanes_per_cell != 32) return TISSUE_E_ARG;
-  if (lanes_per_cell == 16 && V > 256) return TISSUE_E_ARG;
   if (smem_layout != TISSUE_LAYOUT_PREFIX && smem_layout != TISSUE_LAYOUT_RECOMPUTE)
+    return TISSUE_E_ARG;
+  if (smem_layout == TISSUE_LAYOUT_RECOMPUTE && V > lanes_per_cell * lanes_per_cell)
     return TISSUE_E_ARG;
   const bool pre = smem_layout == TISSUE_LAYOUT_PREFIX;
   if (warps_per_block < 1 || warps_per_block > (pre ? 8u : 4u)) return TISSUE_E_ARG;

@@ -383,7 +383,9 @@ int tissue_set_launch_config(tissue* t, const tissue_launch* c) {
     if (c->warps_per_block < 1 || c->warps_per_block > 16) return TISSUE_E_ARG;
   } else if (c->kernel == TISSUE_KERNEL_PERSISTENT) {
     if (c->lanes_per_cell != 32 && c->lanes_per_cell != 16) return TISSUE_E_ARG;
-    if (c->lanes_per_cell == 16 && V > 256) return TISSUE_E_ARG;
+    // the recompute layout needs a block to fit the segment's lanes (V <= lanes^2)
+    if (c->smem_layout == TISSUE_LAYOUT_RECOMPUTE && V > c->lanes_per_cell * c->lanes_per_cell)
+      return TISSUE_E_ARG;
     if (c->smem_layout != TISSUE_LAYOUT_PREFIX && c->smem_layout != TISSUE_LAYOUT_RECOMPUTE)
       return TISSUE_E_ARG;
     const bool pre = c->smem_layout == TISSUE_LAYOUT_PREFIX;

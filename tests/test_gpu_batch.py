@@ -60,7 +60,7 @@ def test_batch_class_launch_shapes_give_the_same_bits():
         members = [T.Tissue(s) for s in MIX]
         b = Batch(members)
         for V in {s.V for s in MIX}:
-            if lanes == 16 and V > 256:
+            if layout == 1 and V > lanes * lanes:
                 continue
             b.set_class_launch(V, lanes, wpb, layout)
         b.step(0.2, 4)
@@ -103,5 +103,7 @@ def test_batch_rejects_bad_input():
         b.set_class_launch(64, 16, 99, 0)
     with pytest.raises(T.TissueError):
         b.set_class_launch(1024, 16, 4, 0)  # no such class
+    with pytest.raises(T.TissueError):
+        b.set_class_launch(64, 4, 2, 1)  # lanes must be 16 or 32
     b.close()
     a.close()

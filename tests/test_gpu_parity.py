@@ -101,27 +101,28 @@ PERSISTENT = [(T.KERNEL_PERSISTENT, 32, 4, 0, T.LAYOUT_PREFIX),
               (T.KERNEL_PERSISTENT, 32, 1, 3, T.LAYOUT_PREFIX),
               (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE),
               (T.KERNEL_PERSISTENT, 32, 2, 0, T.LAYOUT_RECOMPUTE),
-              (T.KERNEL_PERSISTENT, 16, 1, 2, T.LAYOUT_RECOMPUTE)]
+              (T.KERNEL_PERSISTENT, 16, 1, 2, T.LAYOUT_RECOMPUTE),
+              (T.KERNEL_PERSISTENT, 16, 1, 0, T.LAYOUT_PREFIX)]
 
 
 @pytest.mark.parametrize("config", PERSISTENT)
 @pytest.mark.parametrize("w,h,n,dt", [
     (5, 3, 16, 0.1), (3, 2, 10, 0.1), (4, 1, 2, 0.5), (1, 3, 7, 0.2), (7, 5, 8, 1.0),
-    (2, 2, 32, 0.05),
+    (2, 2, 32, 0.05), (3, 2, 30, 0.05), (2, 1, 20, 0.1),
 ])
 def test_persistent_kernel_matches_oracle(config, w, h, n, dt):
     """The persistent work-list kernel, one or two cells per warp, any grid
     (down to a single block pulling every cell), gives the oracle's bits."""
-    if config[1] == 16 and n * n > 256:
-        pytest.skip("16 lanes per cell need V <= 256")
+    if config[4] == T.LAYOUT_RECOMPUTE and n * n > config[1] ** 2:
+        pytest.skip("the recompute layout needs V <= lanes^2")
     spec = TissueSpec(w, h, n, seed=2000 + w * 100 + n, tissue_id=w * h).with_model(**STRONG)
     _run_both(spec, dt, 3, config=config)
 
 
 def test_launch_config_validation():
     g = Tissue(TissueSpec(2, 2, 32, seed=1))
-    with pytest.raises(T.TissueError):
-        g.set_launch_config(T.KERNEL_PERSISTENT, 16, 4, 0)  # V = 1024 needs 32 lanes
+    with pytest.raises(T.TissueError):  # recompute layout: V = 1024 > 16^2
+        g.set_launch_config(T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE)
     with pytest.raises(T.TissueError):
         g.set_launch_config(7, 32, 4, 0)
     with pytest.raises(T.TissueError):

@@ -28,4 +28,6 @@ from .oracle import (  # noqa: F401
     set_paranoid,
     max_threads,
     OracleError,
+    LIE,
+    STRANG,
 )

@@ -155,6 +155,10 @@ def lib():
             L.orc_step.argtypes = [P(_Desc), P(_Model), C.c_void_p, C.c_uint32, C.c_uint32,
                                    C.c_double, C.c_void_p, C.c_void_p, C.c_int]
             L.orc_step.restype = C.c_int
+            L.orc_step_scheme.argtypes = [P(_Desc), P(_Model), C.c_void_p, C.c_uint32,
+                                          C.c_uint32, C.c_double, C.c_int, C.c_void_p,
+                                          C.c_void_p, C.c_int]
+            L.orc_step_scheme.restype = C.c_int
             L.orc_step_traced.argtypes = [P(_Desc), P(_Model), C.c_void_p, C.c_uint32,
                                           C.c_uint32, C.c_double, C.c_void_p, C.c_size_t,
                                           P(C.c_size_t)]
@@ -260,8 +264,11 @@ def sig_face(d: Desc, m: Model, counts: np.ndarray, c: int, axis: int, step: int
     return int(ne.value), float(tl.value)
 
 
+LIE, STRANG = 0, 1
+
+
 def step(d: Desc, m: Model, counts: np.ndarray, step0: int, n_steps: int, dt: float,
-         n_threads: int = 0):
+         n_threads: int = 0, scheme: int = LIE):
     """Run n_steps Lie splitting steps in place.
 
     Returns (n_events[3, cells] uint64, t_last[3, cells] float64) of the last
@@ -271,8 +278,8 @@ def step(d: Desc, m: Model, counts: np.ndarray, step0: int, n_steps: int, dt: fl
     dc, mc = d.to_c(), m.to_c()
     ne = np.zeros((3, d.cells), dtype=np.uint64)
     tl = np.zeros((3, d.cells), dtype=np.float64)
-    rc = lib().orc_step(C.byref(dc), C.byref(mc), _ptr(counts), step0, n_steps, dt,
-                        _ptr(ne), _ptr(tl), n_threads)
+    rc = lib().orc_step_scheme(C.byref(dc), C.byref(mc), _ptr(counts), step0, n_steps, dt,
+                               scheme, _ptr(ne), _ptr(tl), n_threads)
     if rc:
         raise OracleError(rc, "step")
     return ne, tl

@@ -423,13 +423,12 @@ static void face_voxels(int n, int axis, int p, int* va, int* vb) {
 }
 
 static int sig_face_q(const orc_desc* d, const qmodel* q, int32_t* counts, uint32_t c, int axis,
-                      uint32_t step, double dt, uint64_t* n_events, double* t_last,
+                      uint32_t tag, uint32_t step, double dt, uint64_t* n_events, double* t_last,
                       orc_event* trace, size_t cap, size_t* len) {
   const int n = (int)d->n, V = n * n;
   const uint32_t nb = axis == 0 ? c + 1 : c + d->width;
   int32_t* ca = counts + (size_t)c * 3 * V;
   int32_t* cb = counts + (size_t)nb * 3 * V;
-  const uint32_t tag = axis == 0 ? ORC_TAG_SX : ORC_TAG_SY;
   const int nch = 2 * n;
   uint64_t* a = (uint64_t*)malloc(sizeof(uint64_t) * nch);
   if (!a) return ORC_E_ARG;
@@ -494,25 +493,62 @@ int orc_sig_face(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_
   if (c >= d->width * d->height) return ORC_E_ARG;
   if (axis == 0 && cx + 1 >= d->width) return ORC_E_ARG;
   if (axis == 1 && cy + 1 >= d->height) return ORC_E_ARG;
-  return sig_face_q(d, &q, counts, c, axis, step, dt, n_events, t_last, trace, trace_cap,
-                    trace_len);
+  return sig_face_q(d, &q, counts, c, axis, axis == 0 ? ORC_TAG_SX : ORC_TAG_SY, step, dt,
+                    n_events, t_last, trace, trace_cap, trace_len);
 }
 
 /* ------------------------------------------------------------------------ */
-/* One Lie splitting step per k: chi on every cell, then S on every x-face,   */
-/* then S on every y-face.  Within a phase the units touch disjoint voxels,   */
-/* so running them in parallel (OpenMP) cannot change the result.             */
-/* n_events / t_last (optional) receive the LAST step's statistics laid out   */
-/* [3][cells]: row 0 chi per cell, row 1 the x-face owned by the cell, row 2  */
-/* the y-face owned by the cell (0 where the cell owns no such face).         */
-/* ------------------------------------------------------------------------ */
+/* One splitting step per k.
+ *   Lie (scheme 0): chi over dt on every cell, then S over dt on every
+ *     x-face, then on every y-face.
+ *   Strang (scheme 1): S on x-faces over dt/2, S on y-faces over dt/2, chi
+ *     over dt, S on y-faces over dt/2, S on x-faces over dt/2 (the symmetric
+ *     composition; the second halves draw from their own tagged streams).
+ * Within a phase the units touch disjoint voxels, so running them in
+ * parallel (OpenMP) cannot change the result.  n_events / t_last (optional)
+ * receive the LAST step's statistics laid out [3][cells]: row 0 chi per cell,
+ * row 1 the x-face owned by the cell, row 2 its y-face (the last phase of
+ * that axis in the step; 0 where the cell owns no such face). */
+static int face_phase(const orc_desc* d, const qmodel* q, int32_t* counts, int axis, uint32_t tag,
+                      uint32_t k, double dt, int last, uint64_t* n_events, double* t_last,
+                      int n_threads, orc_event* trace, size_t cap, size_t* len) {
+  const int64_t cells = (int64_t)d->width * d->height;
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads) reduction(| : err)
+  for (int64_t c = 0; c < cells; ++c) {
+    const uint32_t cx = (uint32_t)(c % d->width), cy = (uint32_t)(c / d->width);
+    if (axis == 0 && cx + 1 >= d->width) continue;
+    if (axis == 1 && cy + 1 >= d->height) continue;
+    uint64_t ne; double tl;
+    err |= -sig_face_q(d, q, counts, (uint32_t)c, axis, tag, k, dt, &ne, &tl, trace, cap, len);
+    if (last && n_events) n_events[(1 + axis) * cells + c] = ne;
+    if (last && t_last) t_last[(1 + axis) * cells + c] = tl;
+  }
+  return err;
+}
+
+static int chi_phase(const orc_desc* d, const qmodel* q, int32_t* counts, uint32_t k, double dt,
+                     int last, uint64_t* n_events, double* t_last, int n_threads,
+                     orc_event* trace, size_t cap, size_t* len) {
+  const int64_t cells = (int64_t)d->width * d->height;
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads) reduction(| : err)
+  for (int64_t c = 0; c < cells; ++c) {
+    uint64_t ne; double tl;
+    err |= -chi_cell_q(d, q, counts, (uint32_t)c, k, dt, &ne, &tl, trace, cap, len);
+    if (last && n_events) n_events[c] = ne;
+    if (last && t_last) t_last[c] = tl;
+  }
+  return err;
+}
+
 static int step_impl(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_t step0,
-                     uint32_t n_steps, double dt, uint64_t* n_events, double* t_last,
+                     uint32_t n_steps, double dt, int scheme, uint64_t* n_events, double* t_last,
                      int n_threads, orc_event* trace, size_t cap, size_t* len) {
   qmodel q;
   int rc = orc_validate(d, m);
   if (rc) return rc;
-  if (!(dt > 0.0) || !isfinite(dt)) return ORC_E_ARG;
+  if (!(dt > 0.0) || !isfinite(dt) || (scheme != 0 && scheme != 1)) return ORC_E_ARG;
   make_qmodel(m, &q);
   const int64_t cells = (int64_t)d->width * d->height;
 #ifdef _OPENMP
@@ -521,30 +557,30 @@ static int step_impl(const orc_desc* d, const orc_model* m, int32_t* counts, uin
   (void)n_threads;
 #endif
   if (trace) n_threads = 1; /* trace order: unit by unit */
+  const double half = dt * 0.5;
   for (uint32_t s = 0; s < n_steps && rc == ORC_OK; ++s) {
     const uint32_t k = step0 + s;
     const int last = (s + 1 == n_steps);
     if (last && n_events) memset(n_events, 0, sizeof(uint64_t) * 3 * cells);
     if (last && t_last) memset(t_last, 0, sizeof(double) * 3 * cells);
     int err = 0;
-#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads) reduction(| : err)
-    for (int64_t c = 0; c < cells; ++c) {
-      uint64_t ne; double tl;
-      err |= -chi_cell_q(d, &q, counts, (uint32_t)c, k, dt, &ne, &tl, trace, cap, len);
-      if (last && n_events) n_events[c] = ne;
-      if (last && t_last) t_last[c] = tl;
-    }
-    for (int axis = 0; axis < 2 && !err; ++axis) {
-#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads) reduction(| : err)
-      for (int64_t c = 0; c < cells; ++c) {
-        const uint32_t cx = (uint32_t)(c % d->width), cy = (uint32_t)(c / d->width);
-        if (axis == 0 && cx + 1 >= d->width) continue;
-        if (axis == 1 && cy + 1 >= d->height) continue;
-        uint64_t ne; double tl;
-        err |= -sig_face_q(d, &q, counts, (uint32_t)c, axis, k, dt, &ne, &tl, trace, cap, len);
-        if (last && n_events) n_events[(1 + axis) * cells + c] = ne;
-        if (last && t_last) t_last[(1 + axis) * cells + c] = tl;
-      }
+    if (scheme == 0) {
+      err |= chi_phase(d, &q, counts, k, dt, last, n_events, t_last, n_threads, trace, cap, len);
+      if (!err) err |= face_phase(d, &q, counts, 0, ORC_TAG_SX, k, dt, last, n_events, t_last,
+                                  n_threads, trace, cap, len);
+      if (!err) err |= face_phase(d, &q, counts, 1, ORC_TAG_SY, k, dt, last, n_events, t_last,
+                                  n_threads, trace, cap, len);
+    } else {
+      err |= face_phase(d, &q, counts, 0, ORC_TAG_SX, k, half, last, n_events, t_last,
+                        n_threads, trace, cap, len);
+      if (!err) err |= face_phase(d, &q, counts, 1, ORC_TAG_SY, k, half, last, n_events, t_last,
+                                  n_threads, trace, cap, len);
+      if (!err) err |= chi_phase(d, &q, counts, k, dt, last, n_events, t_last, n_threads, trace,
+                                 cap, len);
+      if (!err) err |= face_phase(d, &q, counts, 1, ORC_TAG_SY2, k, half, last, n_events, t_last,
+                                  n_threads, trace, cap, len);
+      if (!err) err |= face_phase(d, &q, counts, 0, ORC_TAG_SX2, k, half, last, n_events, t_last,
+                                  n_threads, trace, cap, len);
     }
     if (err) rc = ORC_E_OVERFLOW;
   }
@@ -553,12 +589,21 @@ static int step_impl(const orc_desc* d, const orc_model* m, int32_t* counts, uin
 
 int orc_step(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_t step0,
              uint32_t n_steps, double dt, uint64_t* n_events, double* t_last, int n_threads) {
-  return step_impl(d, m, counts, step0, n_steps, dt, n_events, t_last, n_threads, NULL, 0, NULL);
+  return step_impl(d, m, counts, step0, n_steps, dt, 0, n_events, t_last, n_threads, NULL, 0,
+                   NULL);
+}
+
+int orc_step_scheme(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_t step0,
+                    uint32_t n_steps, double dt, int scheme, uint64_t* n_events, double* t_last,
+                    int n_threads) {
+  return step_impl(d, m, counts, step0, n_steps, dt, scheme, n_events, t_last, n_threads, NULL,
+                   0, NULL);
 }
 
 int orc_step_traced(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_t step0,
                     uint32_t n_steps, double dt, orc_event* trace, size_t trace_cap,
                     size_t* trace_len) {
   *trace_len = 0;
-  return step_impl(d, m, counts, step0, n_steps, dt, NULL, NULL, 1, trace, trace_cap, trace_len);
+  return step_impl(d, m, counts, step0, n_steps, dt, 0, NULL, NULL, 1, trace, trace_cap,
+                   trace_len);
 }

@@ -44,6 +44,8 @@ extern "C" {
 #define ORC_TAG_SX 2u
 #define ORC_TAG_SY 3u
 #define ORC_TAG_INIT 4u
+#define ORC_TAG_SX2 5u   /* second half-step of x-faces (Strang splitting) */
+#define ORC_TAG_SY2 6u   /* second half-step of y-faces (Strang splitting) */
 
 /* Species index in the state layout counts[cell][species][voxel]. */
 #define ORC_D 0
@@ -94,6 +96,10 @@ int orc_sig_face(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_
                  orc_event* trace, size_t trace_cap, size_t* trace_len);
 int orc_step(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_t step0,
              uint32_t n_steps, double dt, uint64_t* n_events, double* t_last, int n_threads);
+/* scheme 0: Lie (chi, S_x, S_y); 1: Strang (S_x/2, S_y/2, chi, S_y/2, S_x/2). */
+int orc_step_scheme(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_t step0,
+                    uint32_t n_steps, double dt, int scheme, uint64_t* n_events, double* t_last,
+                    int n_threads);
 int orc_step_traced(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_t step0,
                     uint32_t n_steps, double dt, orc_event* trace, size_t trace_cap,
                     size_t* trace_len);

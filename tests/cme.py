@@ -94,8 +94,12 @@ def sig_moves(W, H, n, r, x, axis):
     return out
 
 
-def split_law(W, H, n, rates, x0, dt, k_steps):
-    """Return (states list, index dict, law after k_steps)."""
+def split_law(W, H, n, rates, x0, dt, k_steps, scheme="lie"):
+    """Return (states list, index dict, law after k_steps, generators).
+
+    Lie:    p <- E_Sy(dt) E_Sx(dt) E_chi(dt) p
+    Strang: p <- E_Sx(dt/2) E_Sy(dt/2) E_chi(dt) E_Sy(dt/2) E_Sx(dt/2) p
+    (the rightmost factor acts first)."""
     x0 = tuple(int(v) for v in x0)
     idx = {x0: 0}
     states = [x0]
@@ -121,9 +125,15 @@ def split_law(W, H, n, rates, x0, dt, k_steps):
             M[j, i] += rate
             M[i, i] -= rate
         Q[name] = M
-    P = {name: linalg.expm(M * dt) for name, M in Q.items()}
     p = np.zeros(S)
     p[0] = 1.0
-    for _ in range(k_steps):
-        p = P["sy"] @ (P["sx"] @ (P["chi"] @ p))
+    if scheme == "lie":
+        P = {name: linalg.expm(M * dt) for name, M in Q.items()}
+        for _ in range(k_steps):
+            p = P["sy"] @ (P["sx"] @ (P["chi"] @ p))
+    else:
+        chi = linalg.expm(Q["chi"] * dt)
+        hx, hy = linalg.expm(Q["sx"] * dt / 2), linalg.expm(Q["sy"] * dt / 2)
+        for _ in range(k_steps):
+            p = hx @ (hy @ (chi @ (hy @ (hx @ p))))
     return states, idx, p, Q

@@ -36,21 +36,22 @@ def _initial(W, H, n, axis):
     return x
 
 
-def _ensemble(W, H, n, axis, replicas, dt, k_steps, seed):
+def _ensemble(W, H, n, axis, replicas, dt, k_steps, seed, scheme=O.LIE):
     x0 = _initial(W, H, n, axis)
     m = O.Model(**RATES)
     finals = []
     for r in range(replicas):
         d = O.Desc(W, H, n, seed=seed, tissue_id=r, init_lambda=(0.0, 0.0, 0.0))
         x = x0.copy()
-        O.step(d, m, x, 0, k_steps, dt, n_threads=1)
+        O.step(d, m, x, 0, k_steps, dt, n_threads=1, scheme=scheme)
         finals.append(tuple(int(v) for v in x))
     return x0, finals
 
 
-def _law_pvalue(W, H, n, axis, replicas=12000, dt=0.5, k_steps=3, seed=77):
-    x0, finals = _ensemble(W, H, n, axis, replicas, dt, k_steps, seed)
-    states, idx, p, _ = split_law(W, H, n, _qrates(), x0, dt, k_steps)
+def _law_pvalue(W, H, n, axis, replicas=12000, dt=0.5, k_steps=3, seed=77, scheme=O.LIE):
+    x0, finals = _ensemble(W, H, n, axis, replicas, dt, k_steps, seed, scheme)
+    states, idx, p, _ = split_law(W, H, n, _qrates(), x0, dt, k_steps,
+                                  "lie" if scheme == O.LIE else "strang")
     obs = np.zeros(len(states))
     for f in finals:
         assert f in idx, "oracle reached a state the CME says is unreachable"
@@ -63,6 +64,23 @@ def test_split_process_matches_exact_law(W, H, axis):
     p, S = _law_pvalue(W, H, 2, axis)
     assert S > 100
     assert p > 0.01, p
+
+
+@pytest.mark.parametrize("W,H,axis", [(2, 1, 0), (1, 2, 1)])
+def test_strang_split_process_matches_exact_law(W, H, axis):
+    p, S = _law_pvalue(W, H, 2, axis, seed=79, scheme=O.STRANG)
+    assert p > 0.01, p
+
+
+def test_strang_differs_from_lie_in_law():
+    """The two schemes are different processes at finite dt: the Lie
+    ensemble fails the Strang law."""
+    x0, finals = _ensemble(2, 1, 2, 0, 12000, 1.0, 2, 81, O.LIE)
+    states, idx, p, _ = split_law(2, 1, 2, _qrates(), x0, 1.0, 2, "strang")
+    obs = np.zeros(len(states))
+    for f in finals:
+        obs[idx[f]] += 1
+    assert discrete_gof(obs, p) < 1e-3
 
 
 @pytest.mark.parametrize("mutation", [2, 6])
@@ -82,6 +100,25 @@ def test_face_planted_mistakes_are_caught(mutation):
         else:
             unreachable += 1
     assert unreachable > 0 or discrete_gof(obs, p) < 1e-4
+
+
+def test_strang_splitting_converges_at_second_order():
+    """Strang's symmetric composition is second order: halving dt quarters
+    the distance of the split law from the unsplit law."""
+    x0 = _initial(2, 1, 2, 0)
+    T = 1.0
+    errs = {"lie": [], "strang": []}
+    for scheme in errs:
+        for k in (2, 4, 8, 16):
+            states, idx, p, Q = split_law(2, 1, 2, _qrates(), x0, T / k, k, scheme)
+            p0 = np.zeros(len(states))
+            p0[0] = 1.0
+            exact = linalg.expm((Q["chi"] + Q["sx"] + Q["sy"]) * T) @ p0
+            errs[scheme].append(np.abs(p - exact).sum())
+    r = errs["strang"]
+    ratios = [r[i] / r[i + 1] for i in range(len(r) - 1)]
+    assert ratios == sorted(ratios) and 3.6 < ratios[-1] < 4.4, (r, ratios)  # -> 4
+    assert r[-1] < errs["lie"][-1] / 4
 
 
 def test_lie_splitting_converges_as_dt_shrinks():

@@ -112,10 +112,20 @@ int tissue_write_counts(tissue* t, const int32_t* host, size_t n, uint32_t step_
  * Asynchronous on the tissue's stream; advances the global step index. */
 int tissue_step(tissue* t, double dt, uint32_t n_steps);
 
+/* Splitting scheme of tissue_step (arXiv 1806.10889, Sec. II: modules run one
+ * after the other over dt; the scheme fixes the order).
+ *   TISSUE_SPLIT_LIE (default): chi(dt), S_x(dt), S_y(dt).
+ *   TISSUE_SPLIT_STRANG: S_x(dt/2), S_y(dt/2), chi(dt), S_y(dt/2), S_x(dt/2);
+ *     second order in dt; the second half-steps draw from Philox tags 5 and
+ *     6.  The face rows of tissue_read_stats then hold the last half-step. */
+#define TISSUE_SPLIT_LIE 0u
+#define TISSUE_SPLIT_STRANG 1u
+int tissue_set_splitting(tissue* t, uint32_t scheme);
+
 /* As tissue_step, but also measures the device time of each phase with CUDA
  * events recorded on the tissue's stream around every launch, and waits for
  * the work to finish.  ms_chi receives the summed duration of the chi
- * launches, ms_sig that of the two face phases (either may be NULL). */
+ * launches, ms_sig that of the face phases (either may be NULL). */
 int tissue_step_timed(tissue* t, double dt, uint32_t n_steps, double* ms_chi, double* ms_sig);
 
 /* Copy the state to host memory (n int32 values) after the queued work;
@@ -191,6 +201,9 @@ int tissue_batch_set_class_launch(tissue_batch* b, uint32_t V, uint32_t lanes_pe
  * (1..64, default 1); n_steps not divisible by it end with direct launches. */
 int tissue_batch_set_schedule(tissue_batch* b, uint32_t steps_per_graph);
 
+/* Splitting scheme of the batch's steps (TISSUE_SPLIT_LIE or _STRANG). */
+int tissue_batch_set_splitting(tissue_batch* b, uint32_t scheme);
+
 /* Enqueue n_steps batch steps of length dt on the batch stream. */
 int tissue_batch_step(tissue_batch* b, double dt, uint32_t n_steps);
 
@@ -206,7 +219,7 @@ void tissue_batch_destroy(tissue_batch* b);
 /* Largest tissue (width*height cells) tissue_step_noalloc accepts. */
 #define TISSUE_NOALLOC_MAX_CELLS 16384
 
-/* Allocation-free steps.  The paper has no counterpart; this exists for
+/* Allocation-free steps (Lie splitting).  The paper has no counterpart; this exists for
  * callers that cannot allocate device memory when they advance a tissue (an
  * application that owns a fixed device-memory budget itself, or code where a
  * cudaMalloc would synchronise the device).  No cudaMalloc, cudaFree or

@@ -31,6 +31,10 @@ class Batch:
                                                    smem_layout),
                "tissue_batch_set_class_launch")
 
+    def set_splitting(self, scheme: int):
+        _check(lib().tissue_batch_set_splitting(self._h, int(scheme)),
+               "tissue_batch_set_splitting")
+
     def set_schedule(self, steps_per_graph: int):
         _check(lib().tissue_batch_set_schedule(self._h, int(steps_per_graph)),
                "tissue_batch_set_schedule")

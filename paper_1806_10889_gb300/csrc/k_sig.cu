@@ -22,7 +22,8 @@ namespace {
 
 // The face owned by cell c on `axis`, advanced over [0, dt) by one warp.
 __device__ __forceinline__ void sig_face(const TissueView& t, const uint32_t c, const int axis,
-                                         const uint32_t step_off, const double dt) {
+                                         const uint32_t tag, const uint32_t step_off,
+                                         const double dt) {
   const int lane = threadIdx.x & 31;
   const uint32_t W = t.width, H = t.height;
   const uint32_t nb = axis == 0 ? c + 1 : c + W;
@@ -57,7 +58,7 @@ __device__ __forceinline__ void sig_face(const TissueView& t, const uint32_t c, 
 
   const uint32_t step = *t.step + step_off;
   const uint32_t key0 = static_cast<uint32_t>(t.seed), key1 = static_cast<uint32_t>(t.seed >> 32);
-  const uint32_t word3 = t.tissue_id | ((axis == 0 ? kTagSx : kTagSy) << 24);
+  const uint32_t word3 = t.tissue_id | (tag << 24);
   int err = __any_sync(kFull, ovf) ? kErrOverflow : 0;
   double tnow = 0.0;
   uint32_t e = 0, e0 = 0;
@@ -135,23 +136,24 @@ __device__ __forceinline__ void sig_face(const TissueView& t, const uint32_t c, 
 }
 
 __global__ void __launch_bounds__(256) k_sig(const TissueView t, const int axis,
-                                             const uint32_t step_off, const double dt) {
+                                             const uint32_t tag, const uint32_t step_off,
+                                             const double dt) {
   const uint32_t W = t.width, H = t.height;
   const uint32_t nfaces = axis == 0 ? (W - 1) * H : W * (H - 1);
   const uint32_t f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (f >= nfaces) return;  // whole warp
-  sig_face(t, axis == 0 ? (f / (W - 1)) * W + f % (W - 1) : f, axis, step_off, dt);
+  sig_face(t, axis == 0 ? (f / (W - 1)) * W + f % (W - 1) : f, axis, tag, step_off, dt);
 }
 
 // Faces of many tissues: item = (tissue index, owner cell).
 __global__ void __launch_bounds__(256) k_sig_list(const TissueView* __restrict__ views,
                                                   const uint2* __restrict__ items,
                                                   const uint32_t n_items, const int axis,
-                                                  const double dt) {
+                                                  const uint32_t tag, const double dt) {
   const uint32_t f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (f >= n_items) return;  // whole warp
   const uint2 w = items[f];
-  sig_face(views[w.x], w.y, axis, 0u, dt);
+  sig_face(views[w.x], w.y, axis, tag, 0u, dt);
 }
 
 // Advance the step counter of every tissue of a batch by one.
@@ -200,21 +202,21 @@ __global__ void k_step_advance(uint32_t* step, uint32_t n) {
 
 }  // namespace
 
-cudaError_t launch_sig(const TissueView& t, int axis, uint32_t step_off, double dt,
+cudaError_t launch_sig(const TissueView& t, int axis, uint32_t tag, uint32_t step_off, double dt,
                        cudaStream_t stream) {
   const uint32_t nfaces = axis == 0 ? (t.width - 1) * t.height : t.width * (t.height - 1);
   if (nfaces == 0) return cudaSuccess;
   constexpr int kWarps = 8;
-  k_sig<<<(nfaces + kWarps - 1) / kWarps, 32 * kWarps, 0, stream>>>(t, axis, step_off, dt);
+  k_sig<<<(nfaces + kWarps - 1) / kWarps, 32 * kWarps, 0, stream>>>(t, axis, tag, step_off, dt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sig_list(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
-                            int axis, double dt, cudaStream_t stream) {
+                            int axis, uint32_t tag, double dt, cudaStream_t stream) {
   if (n_items == 0) return cudaSuccess;
   constexpr int kWarps = 8;
   k_sig_list<<<(n_items + kWarps - 1) / kWarps, 32 * kWarps, 0, stream>>>(d_views, d_items, n_items,
-                                                                         axis, dt);
+                                                                         axis, tag, dt);
   return cudaGetLastError();
 }
 

@@ -46,11 +46,12 @@ struct tissue_batch {
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;
   uint32_t steps_per_graph = 1;
+  uint32_t scheme = TISSUE_SPLIT_LIE;
 };
 
 namespace {
 
-int enqueue_step(tissue_batch* b, double dt) {
+int chi_all(tissue_batch* b, double dt) {
   for (size_t c = 0; c < b->classes.size(); ++c) {
     const ClassPlan& p = b->classes[c];
     if (cudaMemsetAsync(b->d_counters + c, 0, sizeof(uint32_t), b->stream) != cudaSuccess)
@@ -60,12 +61,30 @@ int enqueue_step(tissue_batch* b, double dt) {
                        p.layout == TISSUE_LAYOUT_PREFIX, b->stream) != cudaSuccess)
       return TISSUE_E_CUDA;
   }
-  if (launch_sig_list(b->d_views, b->d_items + b->xface_off, b->n_xfaces, 0, dt, b->stream) !=
-          cudaSuccess ||
-      launch_sig_list(b->d_views, b->d_items + b->yface_off, b->n_yfaces, 1, dt, b->stream) !=
-          cudaSuccess ||
-      launch_advance_list(b->d_views, static_cast<uint32_t>(b->members.size()), b->stream) !=
-          cudaSuccess)
+  return TISSUE_OK;
+}
+
+int faces(tissue_batch* b, int axis, uint32_t tag, double dt) {
+  const uint2* items = b->d_items + (axis == 0 ? b->xface_off : b->yface_off);
+  const uint32_t n = axis == 0 ? b->n_xfaces : b->n_yfaces;
+  return launch_sig_list(b->d_views, items, n, axis, tag, dt, b->stream) == cudaSuccess
+             ? TISSUE_OK
+             : TISSUE_E_CUDA;
+}
+
+int enqueue_step(tissue_batch* b, double dt) {
+  int rc;
+  if (b->scheme == TISSUE_SPLIT_LIE) {
+    if ((rc = chi_all(b, dt)) || (rc = faces(b, 0, kTagSx, dt)) || (rc = faces(b, 1, kTagSy, dt)))
+      return rc;
+  } else {
+    const double h = dt * 0.5;
+    if ((rc = faces(b, 0, kTagSx, h)) || (rc = faces(b, 1, kTagSy, h)) || (rc = chi_all(b, dt)) ||
+        (rc = faces(b, 1, kTagSy2, h)) || (rc = faces(b, 0, kTagSx2, h)))
+      return rc;
+  }
+  if (launch_advance_list(b->d_views, static_cast<uint32_t>(b->members.size()), b->stream) !=
+      cudaSuccess)
     return TISSUE_E_CUDA;
   return TISSUE_OK;
 }
@@ -235,6 +254,13 @@ int tissue_batch_set_schedule(tissue_batch* b, uint32_t steps_per_graph) {
   if (!b || steps_per_graph < 1 || steps_per_graph > 64) return TISSUE_E_ARG;
   if (steps_per_graph != b->steps_per_graph) drop_graph(b);
   b->steps_per_graph = steps_per_graph;
+  return TISSUE_OK;
+}
+
+int tissue_batch_set_splitting(tissue_batch* b, uint32_t scheme) {
+  if (!b || (scheme != TISSUE_SPLIT_LIE && scheme != TISSUE_SPLIT_STRANG)) return TISSUE_E_ARG;
+  if (scheme != b->scheme) drop_graph(b);
+  b->scheme = scheme;
   return TISSUE_OK;
 }
 

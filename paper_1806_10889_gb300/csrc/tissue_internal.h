@@ -10,6 +10,7 @@
 namespace tsg {
 
 constexpr uint32_t kTagChi = 1u, kTagSx = 2u, kTagSy = 3u, kTagInit = 4u;
+constexpr uint32_t kTagSx2 = 5u, kTagSy2 = 6u;  // second half-steps of Strang splitting
 constexpr uint32_t kHillTab = 4096;  // tabulated Hill production for R < kHillTab
 constexpr int kErrOverflow = 1;
 constexpr int kErrEventIndex = 2;
@@ -60,7 +61,7 @@ cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint
                            cudaStream_t stream);
 uint32_t seg_bytes_for(uint32_t V, int H, bool pre);
 cudaError_t launch_sig_list(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
-                            int axis, double dt, cudaStream_t stream);
+                            int axis, uint32_t tag, double dt, cudaStream_t stream);
 cudaError_t launch_advance_list(const TissueView* d_views, uint32_t n, cudaStream_t stream);
 
 // Library-internal access to a tissue handle (tissue_lib.cu).
@@ -74,7 +75,8 @@ bool tissue_info(const tissue* t, TissueInfo* out);
 void tissue_advance_host_step(tissue* t, uint32_t n);
 int seg_lanes_for(uint32_t V, int want);
 
-cudaError_t launch_sig(const TissueView& t, int axis, uint32_t step_off, double dt,
+// tag: the Philox stream tag of this face phase (kTagSx, kTagSy, kTagSx2, kTagSy2).
+cudaError_t launch_sig(const TissueView& t, int axis, uint32_t tag, uint32_t step_off, double dt,
                        cudaStream_t stream);
 cudaError_t launch_step_advance(uint32_t* step, uint32_t n, cudaStream_t stream);
 cudaError_t launch_selftest_time(uint64_t n, uint64_t seed, unsigned long long* mismatches,

@@ -33,6 +33,7 @@ struct tissue {
   int* d_err = nullptr;
   uint32_t step_index = 0;
   tissue_launch cfg{TISSUE_KERNEL_WARP, 32, 4, 0, TISSUE_LAYOUT_PREFIX};
+  uint32_t scheme = TISSUE_SPLIT_LIE;
   TissueView* d_view = nullptr;   // device copy of the view, for the persistent kernel
   uint32_t* d_work = nullptr;     // work-list counter of the persistent kernel
 };
@@ -111,6 +112,30 @@ cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt
                           c.smem_layout == TISSUE_LAYOUT_PREFIX, t->stream);
   }
   return launch_chi(v, i, dt, static_cast<int>(c.warps_per_block), t->stream);
+}
+
+// One splitting step at step offset i.  `mark`, if given, is recorded right
+// before and right after the chi launch (for the timed variant).
+int enqueue_split_step(tissue* t, const TissueView& v, uint32_t i, double dt, cudaEvent_t before,
+                       cudaEvent_t after) {
+  auto chi = [&]() -> bool {
+    if (before && cudaEventRecord(before, t->stream) != cudaSuccess) return false;
+    if (launch_chi_cfg(t, v, i, dt) != cudaSuccess) return false;
+    return !after || cudaEventRecord(after, t->stream) == cudaSuccess;
+  };
+  if (t->scheme == TISSUE_SPLIT_LIE) {
+    if (!chi() || launch_sig(v, 0, kTagSx, i, dt, t->stream) != cudaSuccess ||
+        launch_sig(v, 1, kTagSy, i, dt, t->stream) != cudaSuccess)
+      return TISSUE_E_CUDA;
+  } else {
+    const double h = dt * 0.5;
+    if (launch_sig(v, 0, kTagSx, i, h, t->stream) != cudaSuccess ||
+        launch_sig(v, 1, kTagSy, i, h, t->stream) != cudaSuccess || !chi() ||
+        launch_sig(v, 1, kTagSy2, i, h, t->stream) != cudaSuccess ||
+        launch_sig(v, 0, kTagSx2, i, h, t->stream) != cudaSuccess)
+      return TISSUE_E_CUDA;
+  }
+  return TISSUE_OK;
 }
 
 int device_error(tissue* t) {
@@ -271,9 +296,8 @@ int tissue_step(tissue* t, double dt, uint32_t n_steps) {
   if (n_steps == 0) return TISSUE_OK;
   const TissueView v = view_of(t);
   for (uint32_t i = 0; i < n_steps; ++i) {
-    if (launch_chi_cfg(t, v, i, dt) != cudaSuccess) return TISSUE_E_CUDA;
-    if (launch_sig(v, 0, i, dt, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
-    if (launch_sig(v, 1, i, dt, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+    const int rc = enqueue_split_step(t, v, i, dt, nullptr, nullptr);
+    if (rc != TISSUE_OK) return rc;
   }
   if (launch_step_advance(t->d_step, n_steps, t->stream) != cudaSuccess) return TISSUE_E_CUDA;
   t->step_index += n_steps;
@@ -284,41 +308,43 @@ int tissue_step_timed(tissue* t, double dt, uint32_t n_steps, double* ms_chi, do
   if (!t) return TISSUE_E_ARG;
   if (!t->has_model) return TISSUE_E_NOMODEL;
   if (!(dt > 0.0) || !std::isfinite(dt)) return TISSUE_E_ARG;
-  // marks[0] before the first launch; marks[2i+1] after chi of step i,
-  // marks[2i+2] after both face phases of step i.
-  std::vector<cudaEvent_t> marks(2 * static_cast<size_t>(n_steps) + 1, nullptr);
+  // per step: start, chi start, chi end, end
+  std::vector<cudaEvent_t> ev(4 * static_cast<size_t>(n_steps), nullptr);
   int rc = TISSUE_OK;
-  for (auto& e : marks)
+  for (auto& e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) rc = TISSUE_E_CUDA;
   const TissueView v = view_of(t);
-  if (rc == TISSUE_OK && cudaEventRecord(marks[0], t->stream) != cudaSuccess) rc = TISSUE_E_CUDA;
   for (uint32_t i = 0; i < n_steps && rc == TISSUE_OK; ++i) {
-    if (launch_chi_cfg(t, v, i, dt) != cudaSuccess ||
-        cudaEventRecord(marks[2 * i + 1], t->stream) != cudaSuccess ||
-        launch_sig(v, 0, i, dt, t->stream) != cudaSuccess ||
-        launch_sig(v, 1, i, dt, t->stream) != cudaSuccess ||
-        cudaEventRecord(marks[2 * i + 2], t->stream) != cudaSuccess)
+    if (cudaEventRecord(ev[4 * i], t->stream) != cudaSuccess) rc = TISSUE_E_CUDA;
+    if (rc == TISSUE_OK) rc = enqueue_split_step(t, v, i, dt, ev[4 * i + 1], ev[4 * i + 2]);
+    if (rc == TISSUE_OK && cudaEventRecord(ev[4 * i + 3], t->stream) != cudaSuccess)
       rc = TISSUE_E_CUDA;
   }
   if (rc == TISSUE_OK && launch_step_advance(t->d_step, n_steps, t->stream) != cudaSuccess)
     rc = TISSUE_E_CUDA;
   if (rc == TISSUE_OK && cudaStreamSynchronize(t->stream) != cudaSuccess) rc = TISSUE_E_CUDA;
-  double chi = 0.0, sig = 0.0;
+  double chi = 0.0, all = 0.0;
   for (uint32_t i = 0; i < n_steps && rc == TISSUE_OK; ++i) {
     float a = 0.f, b = 0.f;
-    if (cudaEventElapsedTime(&a, marks[2 * i], marks[2 * i + 1]) != cudaSuccess ||
-        cudaEventElapsedTime(&b, marks[2 * i + 1], marks[2 * i + 2]) != cudaSuccess)
+    if (cudaEventElapsedTime(&a, ev[4 * i + 1], ev[4 * i + 2]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, ev[4 * i], ev[4 * i + 3]) != cudaSuccess)
       rc = TISSUE_E_CUDA;
     chi += a;
-    sig += b;
+    all += b;
   }
-  for (auto& e : marks)
+  for (auto& e : ev)
     if (e) cudaEventDestroy(e);
   if (rc != TISSUE_OK) return rc;
   t->step_index += n_steps;
   if (ms_chi) *ms_chi = chi;
-  if (ms_sig) *ms_sig = sig;
+  if (ms_sig) *ms_sig = all - chi;
   return device_error(t);
+}
+
+int tissue_set_splitting(tissue* t, uint32_t scheme) {
+  if (!t || (scheme != TISSUE_SPLIT_LIE && scheme != TISSUE_SPLIT_STRANG)) return TISSUE_E_ARG;
+  t->scheme = scheme;
+  return TISSUE_OK;
 }
 
 int tissue_read_counts(tissue* t, int32_t* host, size_t n) {

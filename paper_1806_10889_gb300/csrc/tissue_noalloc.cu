@@ -119,8 +119,8 @@ extern "C" int tissue_step_noalloc(const tissue_desc* d, const tissue_model* m,
   if (launch_hill_table(q, s->hill, stream) != cudaSuccess) return TISSUE_E_CUDA;
   for (uint32_t i = 0; i < n_steps; ++i) {
     if (launch_chi(v, i, dt, 4, stream) != cudaSuccess) return TISSUE_E_CUDA;
-    if (launch_sig(v, 0, i, dt, stream) != cudaSuccess) return TISSUE_E_CUDA;
-    if (launch_sig(v, 1, i, dt, stream) != cudaSuccess) return TISSUE_E_CUDA;
+    if (launch_sig(v, 0, kTagSx, i, dt, stream) != cudaSuccess) return TISSUE_E_CUDA;
+    if (launch_sig(v, 1, kTagSy, i, dt, stream) != cudaSuccess) return TISSUE_E_CUDA;
   }
   int flag = 0;
   if (cudaMemcpyAsync(&flag, &s->err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess)

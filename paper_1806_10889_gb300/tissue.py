@@ -48,6 +48,7 @@ class Model(C.Structure):
 
 KERNEL_WARP, KERNEL_PERSISTENT = 0, 1
 LAYOUT_PREFIX, LAYOUT_RECOMPUTE = 0, 1
+SPLIT_LIE, SPLIT_STRANG = 0, 1
 
 
 class Launch(C.Structure):
@@ -73,6 +74,8 @@ SIGNATURES = {
     "tissue_get_step": (C.c_int, [C.c_void_p, _P(C.c_uint32)]),
     "tissue_sync": (C.c_int, [C.c_void_p]),
     "tissue_set_launch": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "tissue_set_splitting": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "tissue_batch_set_splitting": (C.c_int, [C.c_void_p, C.c_uint32]),
     "tissue_set_launch_config": (C.c_int, [C.c_void_p, _P(Launch)]),
     "tissue_get_launch_config": (C.c_int, [C.c_void_p, _P(Launch)]),
     "tissue_step_noalloc": (C.c_int, [_P(Desc), _P(Model), C.c_void_p, C.c_uint32, C.c_double,
@@ -206,6 +209,9 @@ class Tissue:
         c = Launch()
         _check(lib().tissue_get_launch_config(self._h, C.byref(c)), "tissue_get_launch_config")
         return (c.kernel, c.lanes_per_cell, c.warps_per_block, c.blocks, c.smem_layout)
+
+    def set_splitting(self, scheme: int):
+        _check(lib().tissue_set_splitting(self._h, int(scheme)), "tissue_set_splitting")
 
     def step(self, dt: float, n_steps: int = 1):
         _check(lib().tissue_step(self._h, float(dt), int(n_steps)), "tissue_step")

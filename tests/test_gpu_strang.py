@@ -1,0 +1,78 @@
+"""Strang splitting on the GPU, bit for bit against the oracle's Strang
+scheme (whose law is pinned to the exact CME of the Strang-split process),
+for single tissues in several launch shapes and for a batch."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_10889_gb300.workloads import TissueSpec
+from tests._util import orc_desc, orc_model
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1806_10889_gb300 import tissue as T  # noqa: E402
+from paper_1806_10889_gb300.batching import Batch  # noqa: E402
+
+
+def _bits(x):
+    return np.asarray(x, dtype=np.float64).view(np.uint64)
+
+
+@pytest.mark.parametrize("config", [None, (T.KERNEL_WARP, 32, 4, 0, 0),
+                                    (T.KERNEL_PERSISTENT, 16, 2, 0, 1)])
+@pytest.mark.parametrize("w,h,n,dt", [(4, 3, 8, 0.2), (3, 3, 16, 0.1), (2, 2, 32, 0.05),
+                                      (5, 1, 6, 0.5)])
+def test_strang_matches_oracle(config, w, h, n, dt):
+    if config and config[4] == T.LAYOUT_RECOMPUTE and n * n > config[1] ** 2:
+        pytest.skip("the recompute layout needs V <= lanes^2")
+    spec = TissueSpec(w, h, n, seed=500 + n, tissue_id=7).with_model(k_bind=0.05)
+    d, m = orc_desc(spec), orc_model(spec)
+    ref = O.init_counts(d)
+    g = T.Tissue(spec)
+    g.set_splitting(T.SPLIT_STRANG)
+    if config:
+        g.set_launch_config(*config)
+    for k in range(3):
+        ne, tl = O.step(d, m, ref, k, 1, dt, scheme=O.STRANG)
+        g.step(dt, 1)
+        assert np.array_equal(g.read_counts(), ref), k
+        gne, gtl = g.read_stats()
+        assert np.array_equal(gne, ne) and np.array_equal(_bits(gtl), _bits(tl)), k
+    g.close()
+
+
+def test_strang_and_lie_differ_and_timed_step_agrees():
+    spec = TissueSpec(3, 3, 8, seed=77).with_model(k_bind=0.05)
+    a, b, c = T.Tissue(spec), T.Tissue(spec), T.Tissue(spec)
+    b.set_splitting(T.SPLIT_STRANG)
+    c.set_splitting(T.SPLIT_STRANG)
+    a.step(0.2, 2)
+    b.step(0.2, 2)
+    ms_chi, ms_sig = c.step_timed(0.2, 2)
+    assert ms_chi > 0 and ms_sig > 0
+    assert not np.array_equal(a.read_counts(), b.read_counts())
+    assert np.array_equal(b.read_counts(), c.read_counts())
+    for t in (a, b, c):
+        t.close()
+
+
+def test_batch_strang_matches_oracle():
+    specs = [TissueSpec(3, 2, 8, seed=3, tissue_id=0),
+             TissueSpec(2, 3, 16, seed=3, tissue_id=1).with_model(kD=15.0, k_bind=0.05),
+             TissueSpec(2, 2, 32, seed=3, tissue_id=2)]
+    members = [T.Tissue(s) for s in specs]
+    bt = Batch(members)
+    bt.set_splitting(T.SPLIT_STRANG)
+    bt.step(0.1, 3)
+    bt.sync()
+    for s, mbr in zip(specs, members):
+        ref = O.init_counts(orc_desc(s))
+        O.step(orc_desc(s), orc_model(s), ref, 0, 3, 0.1, scheme=O.STRANG)
+        assert np.array_equal(mbr.read_counts(), ref)
+    bt.close()
+    for mbr in members:
+        mbr.close()

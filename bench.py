@@ -437,7 +437,7 @@ def main():
     ap.add_argument("--burn-in", type=float, default=20.0, help="untimed simulated time first")
     ap.add_argument("--chi-wpb", type=int, default=0)
     ap.add_argument("--kernel", choices=["default", "warp", "persistent"], default="default")
-    ap.add_argument("--lanes", type=int, choices=[16, 32], default=16)
+    ap.add_argument("--lanes", type=int, choices=[8, 16, 32], default=16)
     ap.add_argument("--layout", type=int, choices=[0, 1], default=0,
                     help="persistent kernel: 0 prefix arrays, 1 recompute")
     ap.add_argument("--chi-traffic", type=float, default=None,

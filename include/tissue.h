@@ -161,13 +161,14 @@ int tissue_set_launch(tissue* t, uint32_t chi_warps_per_block);
 #define TISSUE_LAYOUT_RECOMPUTE 1u /* counts only (12 B/voxel); <= 4 warps per block, V <= lanes^2 */
 typedef struct {
   uint32_t kernel;          /* TISSUE_KERNEL_WARP or TISSUE_KERNEL_PERSISTENT */
-  uint32_t lanes_per_cell;  /* persistent kernel: 32, or 16 (two cells per warp) */
+  uint32_t lanes_per_cell;  /* persistent kernel: 32, 16 or 8 (1, 2 or 4 cells per warp) */
   uint32_t warps_per_block; /* 1..16 (warp kernel) or 1..8 (persistent kernel) */
   uint32_t blocks;          /* persistent kernel grid; 0 = enough to fill every SM */
   uint32_t smem_layout;     /* persistent kernel: TISSUE_LAYOUT_PREFIX or _RECOMPUTE */
 } tissue_launch;
-/* The default after tissue_create: persistent, 16 lanes, 4 warps per block for
- * cells of at most 256 voxels; otherwise the warp kernel, 4 warps per block. */
+/* The default after tissue_create, by cell size: persistent kernel, prefix
+ * layout, with 8 lanes and 4 warps per block for V <= 64, 16 lanes and 4
+ * warps for V <= 256, 32 lanes and 2 warps above. */
 int tissue_set_launch_config(tissue* t, const tissue_launch* config);
 int tissue_get_launch_config(const tissue* t, tissue_launch* config);
 
@@ -190,10 +191,9 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
                         tissue_batch** out);
 
 /* Launch shape of the chi launch of the class of cells with V voxels:
- * 16 or 32 lanes per cell, 1..8 warps per block (1..4 with the recompute
+ * 8, 16 or 32 lanes per cell, 1..8 warps per block (1..4 with the recompute
  * layout, which also needs V <= lanes^2), shared-memory layout TISSUE_LAYOUT_*.  The default is
- * 16 lanes where allowed, 4 warps per block, prefix layout.  Results never
- * depend on it. */
+ * the single-tissue default for that V.  Results never depend on it. */
 int tissue_batch_set_class_launch(tissue_batch* b, uint32_t V, uint32_t lanes_per_cell,
                                   uint32_t warps_per_block, uint32_t smem_layout);
 

@@ -16,7 +16,8 @@ import threading
 
 import numpy as np
 
-from .tissue import KERNEL_PERSISTENT, KERNEL_WARP, LAYOUT_PREFIX, LAYOUT_RECOMPUTE, Tissue
+from .tissue import (KERNEL_PERSISTENT, KERNEL_WARP, LAYOUT_PREFIX, LAYOUT_RECOMPUTE, Tissue,
+                     TissueError)
 from .workloads import TissueSpec
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
@@ -31,7 +32,7 @@ def tissue_candidates(V: int) -> list[tuple]:
     """(kernel, lanes per cell, warps per block, blocks, shared-memory layout)
     candidates for cells of V voxels."""
     c = [(KERNEL_WARP, 32, w, 0, LAYOUT_PREFIX) for w in (2, 4, 8)]
-    for lanes in (16, 32):
+    for lanes in (8, 16, 32):
         c += [(KERNEL_PERSISTENT, lanes, w, 0, LAYOUT_PREFIX) for w in (1, 2, 4)]
         if V <= lanes * lanes:
             c += [(KERNEL_PERSISTENT, lanes, w, 0, LAYOUT_RECOMPUTE) for w in (2, 4)]
@@ -41,7 +42,7 @@ def tissue_candidates(V: int) -> list[tuple]:
 def batch_class_candidates(V: int) -> list[tuple]:
     """(lanes per cell, warps per block, layout) candidates for one cell-size class."""
     c = []
-    for lanes in (16, 32):
+    for lanes in (8, 16, 32):
         c += [(lanes, w, LAYOUT_PREFIX) for w in (1, 2, 4)]
         if V <= lanes * lanes:
             c += [(lanes, w, LAYOUT_RECOMPUTE) for w in (2, 4)]
@@ -99,12 +100,17 @@ def tune_tissue(spec: TissueSpec, dt: float, state: np.ndarray | None = None,
         if hit:
             return {"config": tuple(hit["config"]), "ms": hit["ms"], "cached": True}
     cands = candidates or tissue_candidates(spec.V)
-    times, ref = {}, None
+    times, ref, tried = {}, None, []
     for cfg in cands:
         t = Tissue(spec)
         if state is not None:
             t.write_counts(state, step_index)
-        t.set_launch_config(*cfg)
+        try:
+            t.set_launch_config(*cfg)
+        except TissueError:  # the shape does not fit these cells (shared memory)
+            t.close()
+            continue
+        tried.append(cfg)
         t.step(dt, 1)  # warm (first launch of a variant configures it)
         t.sync()
         times[str(cfg)] = _time_steps(lambda n: t.step(dt, n), steps)
@@ -116,7 +122,7 @@ def tune_tissue(spec: TissueSpec, dt: float, state: np.ndarray | None = None,
             t.close()
             raise VariantMismatch(f"launch {cfg} changed the trajectory of {spec}")
         t.close()
-    best = min(cands, key=lambda c: times[str(c)])
+    best = min(tried, key=lambda c: times[str(c)])
     result = {"config": list(best), "ms": times}
     _store(key, result)
     return {"config": tuple(best), "ms": times, "cached": False}
@@ -155,11 +161,18 @@ def tune_batch(members: list[Tissue], dt: float, steps: int = 1, max_clones: int
 
     chosen, timings = {}, {}
     for V, ms in sorted(by_v.items()):
-        ref = None
+        ref, tried = None, []
         for lanes, wpb, layout in batch_class_candidates(V):
             clones = clones_of(ms)
             b = Batch(clones)
-            b.set_class_launch(V, lanes, wpb, layout)
+            try:
+                b.set_class_launch(V, lanes, wpb, layout)
+            except TissueError:  # does not fit shared memory for this V
+                b.close()
+                for c in clones:
+                    c.close()
+                continue
+            tried.append((lanes, wpb, layout))
             b.step(dt, 1)
             b.sync()
             ms_ = _time_steps(lambda n: b.step(dt, n), steps, b.stream)
@@ -173,8 +186,7 @@ def tune_batch(members: list[Tissue], dt: float, steps: int = 1, max_clones: int
             b.close()
             for c in clones:
                 c.close()
-        chosen[V] = min(batch_class_candidates(V),
-                        key=lambda c: timings[f"{V}:{c[0]}x{c[1]}/{c[2]}"])
+        chosen[V] = min(tried, key=lambda c: timings[f"{V}:{c[0]}x{c[1]}/{c[2]}"])
     # schedule: tune on a clone of the whole (bounded) batch with the chosen classes
     best_k, best_ms = 1, None
     for k in schedules:

@@ -87,6 +87,17 @@ __device__ __forceinline__ ChanLane chan_lane(int j) {
 // pre[] of the voxel propensities (20 B per voxel); false keeps only the
 // counts (12 B per voxel) and recomputes the selected block's propensities,
 // trading ~70 instructions per pass for ~40% more cells resident per SM.
+// Running sum C_j of the channels 0..j of a voxel (~0 for j >= 19).
+__device__ __forceinline__ uint64_t chan_cum(const ChanLane& c, const QRates& q, uint64_t hill,
+                                             uint32_t D, uint32_t N, uint32_t R, uint64_t DN,
+                                             uint32_t hm) {
+  if (!c.valid) return ~0ull;
+  return hill + (c.f1 ? q.kN : 0ull) + D * ((c.f2 ? q.gD : 0ull) + q.hopD * __popc(hm & c.mD)) +
+         N * ((c.f3 ? q.gN : 0ull) + q.hopN * __popc(hm & c.mN)) +
+         R * ((c.f4 ? q.gR : 0ull) + q.hopR * __popc(hm & c.mR) + (c.f18 ? q.k_off : 0ull)) +
+         (c.f17 ? q.k_in * DN : 0ull);
+}
+
 template <int H, bool LIST, bool PRE>
 __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
                                                  const TissueView* __restrict__ views,
@@ -98,7 +109,8 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int seg = lane / H, sl = lane % H;
-  const unsigned segmask = H == 32 ? kFull : (0xFFFFu << (16 * seg));
+  constexpr unsigned kSegBits = H == 32 ? kFull : ((1u << H) - 1u);
+  const unsigned segmask = H == 32 ? kFull : (kSegBits << (H * seg));
   unsigned char* base = smem + static_cast<size_t>(wib * G + seg) * seg_bytes;
   TissueView* sv = reinterpret_cast<TissueView*>(base);
   constexpr int kBytesPerVoxel = PRE ? 20 : 12;
@@ -106,6 +118,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
   uint64_t* pre = reinterpret_cast<uint64_t*>(base + kViewBytes);  // used only if PRE
   int32_t* cnt = reinterpret_cast<int32_t*>(base + kViewBytes + (PRE ? 8 * vmax : 0));
   const ChanLane cl = chan_lane(sl);
+  const ChanLane cl2 = chan_lane(sl + H);  // second channel of each lane when H = 8
 
   bool have = false, done = false;
   Seg s{0, 2, 1, 0, 1, 0};
@@ -231,7 +244,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     const double tn = __dadd_rn(tnow, tau_from(F53{mE, kE}, kE < 0 || Aa == 0ull, Aa | (Aa == 0ull)));
 
     const uint64_t r = __umul64hi(R64, Aa);
-    const unsigned m1 = (__ballot_sync(kFull, r < P && act) >> (seg * H)) & (H == 32 ? kFull : 0xFFFFu);
+    const unsigned m1 = (__ballot_sync(kFull, r < P && act) >> (seg * H)) & kSegBits;
     const int L = m1 ? __ffs(m1) - 1 : 0;
     const uint64_t Pl = __shfl_sync(kFull, P, L > 0 ? L - 1 : 0, H);
     const uint64_t r1 = r - (L > 0 ? Pl : 0ull);
@@ -254,7 +267,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
       }
       if (sl < s.B && vb + sl < s.V) pv = cx;
     }
-    const unsigned m2 = (__ballot_sync(kFull, r1 < pv) >> (seg * H)) & (H == 32 ? kFull : 0xFFFFu);
+    const unsigned m2 = (__ballot_sync(kFull, r1 < pv) >> (seg * H)) & kSegBits;
     const int i2 = m2 ? __ffs(m2) - 1 : 0;
     const uint64_t pp = __shfl_sync(kFull, pv, i2 > 0 ? i2 - 1 : 0, H);
     uint64_t r2 = r1 - (i2 > 0 ? pp : 0ull);
@@ -289,23 +302,23 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     const uint32_t hm = dir_mask(v, s);
     const uint64_t hill = act ? hill_q(q, R) : 0ull;  // no table read for an idle segment
     const uint64_t DN = static_cast<uint64_t>(D) * N;
-    uint64_t C = hill + (cl.f1 ? q.kN : 0ull) +
-                 D * ((cl.f2 ? q.gD : 0ull) + q.hopD * __popc(hm & cl.mD)) +
-                 N * ((cl.f3 ? q.gN : 0ull) + q.hopN * __popc(hm & cl.mN)) +
-                 R * ((cl.f4 ? q.gR : 0ull) + q.hopR * __popc(hm & cl.mR) + (cl.f18 ? q.k_off : 0ull)) +
-                 (cl.f17 ? q.k_in * DN : 0ull);
-    if (!cl.valid) C = ~0ull;
+    const uint64_t C = chan_cum(cl, q, hill, D, N, R, DN, hm);
+    const uint64_t Cb = H == 8 ? chan_cum(cl2, q, hill, D, N, R, DN, hm) : ~0ull;
     uint64_t C16 = 0, C17 = 0, C18;
-    if (H == 16) {
-      const uint64_t C15 = __shfl_sync(kFull, C, 15, H);
+    if (H <= 16) {
+      // C_16..C_18 from C_15: +x hop of R (if that neighbour exists), D+N->R, R->D+N
+      const uint64_t C15 = __shfl_sync(kFull, H == 16 ? C : Cb, H == 16 ? 15 : 7, H);
       C16 = C15 + (((hm >> 3) & 1u) ? q.hopR * R : 0ull);
       C17 = C16 + q.k_in * DN;
       C18 = C17 + q.k_off * R;
     } else {
       C18 = __shfl_sync(kFull, C, 18, H);
     }
-    const unsigned m3 = (__ballot_sync(kFull, r2 < C) >> (seg * H)) & (H == 32 ? kFull : 0xFFFFu);
-    int ch = m3 ? __ffs(m3) - 1 : 16 + static_cast<int>(r2 >= C16) + static_cast<int>(r2 >= C17);
+    const unsigned m3 = (__ballot_sync(kFull, r2 < C) >> (seg * H)) & kSegBits;
+    const unsigned m3b = H == 8 ? (__ballot_sync(kFull, r2 < Cb) >> (seg * H)) & kSegBits : 0u;
+    int ch = m3 ? __ffs(m3) - 1
+                : m3b ? H + __ffs(m3b) - 1
+                      : 16 + static_cast<int>(r2 >= C16) + static_cast<int>(r2 >= C17);
     const bool bad = bad1 || (act && Aa != 0ull && !(r2 < C18));
     const uint64_t a_old_v = C18;
     if (ch > 18) ch = 18;
@@ -399,7 +412,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     __syncwarp();
 
     // ---- a segment whose cell is finished writes it back ------------------
-    const unsigned seg_err = (__ballot_sync(kFull, err != 0) >> (seg * H)) & (H == 32 ? kFull : 0xFFFFu);
+    const unsigned seg_err = (__ballot_sync(kFull, err != 0) >> (seg * H)) & kSegBits;
     const bool finish = act && (!fire_ok || seg_err != 0u);
     if (finish) {
       if ((s.V & 3) == 0) {
@@ -450,7 +463,10 @@ cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint
   const size_t smem = static_cast<size_t>(warps_per_block) * (32 / H) * seg_bytes;
   const int threads = 32 * warps_per_block;
   void (*k)(const TissueView*, const uint2*, uint32_t, uint32_t*, uint32_t, uint32_t, double);
-  if (H == 16) {
+  if (H == 8) {
+    if (pre) k = d_items ? k_chi_seg<8, true, true> : k_chi_seg<8, false, true>;
+    else k = d_items ? k_chi_seg<8, true, false> : k_chi_seg<8, false, false>;
+  } else if (H == 16) {
     if (pre) k = d_items ? k_chi_seg<16, true, true> : k_chi_seg<16, false, true>;
     else k = d_items ? k_chi_seg<16, true, false> : k_chi_seg<16, false, false>;
   } else {

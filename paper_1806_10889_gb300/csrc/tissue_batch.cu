@@ -133,9 +133,10 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
   for (auto& kv : by_v) {
     ClassPlan p{};
     p.V = kv.first;
-    p.lanes = kv.first <= 256 ? 16u : 32u;
-    p.warps_per_block = 4;
-    p.layout = TISSUE_LAYOUT_PREFIX;
+    const tissue_launch dl = default_launch(kv.first);
+    p.lanes = dl.lanes_per_cell;
+    p.warps_per_block = dl.warps_per_block;
+    p.layout = dl.smem_layout;
     p.items_off = items.size();
     p.n_items = static_cast<uint32_t>(kv.second.size());
     items.insert(items.end(), kv.second.begin(), kv.second.end());
@@ -184,7 +185,7 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
 int tissue_batch_set_class_launch(tissue_batch* b, uint32_t V, uint32_t lanes_per_cell,
                                   uint32_t warps_per_block, uint32_t smem_layout) {
   if (!b) return TISSUE_E_ARG;
-  if (lanes_per_cell != 16 && lanes_per_cell != 32) return TISSUE_E_ARG;
+  if (lanes_per_cell != 8 && lanes_per_cell != 16 && lanes_per_cell != 32) return TISSUE_E_ARG;
   if (smem_layout != TISSUE_LAYOUT_PREFIX && smem_layout != TISSUE_LAYOUT_RECOMPUTE)
     return TISSUE_E_ARG;
   if (smem_layout == TISSUE_LAYOUT_RECOMPUTE && V > lanes_per_cell * lanes_per_cell)

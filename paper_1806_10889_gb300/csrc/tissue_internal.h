@@ -72,6 +72,8 @@ struct TissueInfo {
   bool has_model;
 };
 bool tissue_info(const tissue* t, TissueInfo* out);
+// The default chi launch for cells of V voxels.
+tissue_launch default_launch(uint32_t V);
 void tissue_advance_host_step(tissue* t, uint32_t n);
 int seg_lanes_for(uint32_t V, int want);
 

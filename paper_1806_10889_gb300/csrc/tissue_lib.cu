@@ -100,6 +100,16 @@ TissueView view_of(const tissue* t) {
   return v;
 }
 
+}  // namespace
+
+tissue_launch tsg::default_launch(uint32_t V) {
+  if (V <= 64) return tissue_launch{TISSUE_KERNEL_PERSISTENT, 8, 4, 0, TISSUE_LAYOUT_PREFIX};
+  if (V <= 256) return tissue_launch{TISSUE_KERNEL_PERSISTENT, 16, 4, 0, TISSUE_LAYOUT_PREFIX};
+  return tissue_launch{TISSUE_KERNEL_PERSISTENT, 32, 2, 0, TISSUE_LAYOUT_PREFIX};
+}
+
+namespace {
+
 // chi for step offset i, in the tissue's launch configuration.
 cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt) {
   const tissue_launch& c = t->cfg;
@@ -219,10 +229,10 @@ int tissue_create(const tissue_desc* d, void* dev_counts, size_t bytes, void* cu
   t->counts = static_cast<int32_t*>(dev_counts);
   t->bytes = bytes;
   t->stream = static_cast<cudaStream_t>(cuda_stream);
-  // Default chi launch: two cells per warp on the persistent kernel where a
-  // cell fits 16 lanes (V <= 256), otherwise one warp per cell.
-  if (d->n * d->n <= 256)
-    t->cfg = tissue_launch{TISSUE_KERNEL_PERSISTENT, 16, 4, 0, TISSUE_LAYOUT_PREFIX};
+  // Default chi launch (measured on GB300): the persistent kernel with four
+  // cells per warp for V <= 64, two for V <= 256, one (2 warps per block)
+  // above.
+  t->cfg = default_launch(d->n * d->n);
   const ScratchLayout L = layout(d);
   if (cudaMalloc(&t->scratch, L.total) != cudaSuccess) {
     cudaGetLastError();
@@ -408,7 +418,8 @@ int tissue_set_launch_config(tissue* t, const tissue_launch* c) {
   if (c->kernel == TISSUE_KERNEL_WARP) {
     if (c->warps_per_block < 1 || c->warps_per_block > 16) return TISSUE_E_ARG;
   } else if (c->kernel == TISSUE_KERNEL_PERSISTENT) {
-    if (c->lanes_per_cell != 32 && c->lanes_per_cell != 16) return TISSUE_E_ARG;
+    if (c->lanes_per_cell != 32 && c->lanes_per_cell != 16 && c->lanes_per_cell != 8)
+      return TISSUE_E_ARG;
     // the recompute layout needs a block to fit the segment's lanes (V <= lanes^2)
     if (c->smem_layout == TISSUE_LAYOUT_RECOMPUTE && V > c->lanes_per_cell * c->lanes_per_cell)
       return TISSUE_E_ARG;

@@ -102,7 +102,10 @@ PERSISTENT = [(T.KERNEL_PERSISTENT, 32, 4, 0, T.LAYOUT_PREFIX),
               (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE),
               (T.KERNEL_PERSISTENT, 32, 2, 0, T.LAYOUT_RECOMPUTE),
               (T.KERNEL_PERSISTENT, 16, 1, 2, T.LAYOUT_RECOMPUTE),
-              (T.KERNEL_PERSISTENT, 16, 1, 0, T.LAYOUT_PREFIX)]
+              (T.KERNEL_PERSISTENT, 16, 1, 0, T.LAYOUT_PREFIX),
+              (T.KERNEL_PERSISTENT, 8, 4, 0, T.LAYOUT_PREFIX),
+              (T.KERNEL_PERSISTENT, 8, 2, 0, T.LAYOUT_RECOMPUTE),
+              (T.KERNEL_PERSISTENT, 8, 1, 1, T.LAYOUT_PREFIX)]
 
 
 @pytest.mark.parametrize("config", PERSISTENT)
@@ -111,10 +114,17 @@ PERSISTENT = [(T.KERNEL_PERSISTENT, 32, 4, 0, T.LAYOUT_PREFIX),
     (2, 2, 32, 0.05), (3, 2, 30, 0.05), (2, 1, 20, 0.1),
 ])
 def test_persistent_kernel_matches_oracle(config, w, h, n, dt):
-    """The persistent work-list kernel, one or two cells per warp, any grid
-    (down to a single block pulling every cell), gives the oracle's bits."""
+    """The persistent work-list kernel, one, two or four cells per warp, any
+    grid (down to a single block pulling every cell), gives the oracle's bits."""
     if config[4] == T.LAYOUT_RECOMPUTE and n * n > config[1] ** 2:
         pytest.skip("the recompute layout needs V <= lanes^2")
+    lanes, wpb = config[1], config[2]
+    blocks_v = 1
+    while lanes * blocks_v < n * n:
+        blocks_v *= 2
+    per_voxel = 20 if config[4] == T.LAYOUT_PREFIX else 12
+    if wpb * (32 // lanes) * (512 + per_voxel * lanes * blocks_v) > 227 * 1024:
+        pytest.skip("this launch shape does not fit shared memory for these cells")
     spec = TissueSpec(w, h, n, seed=2000 + w * 100 + n, tissue_id=w * h).with_model(**STRONG)
     _run_both(spec, dt, 3, config=config)
 
@@ -134,14 +144,16 @@ def test_launch_config_validation():
 
 @pytest.mark.parametrize("config", [None, (T.KERNEL_PERSISTENT, 16, 4, 0),
                                     (T.KERNEL_PERSISTENT, 32, 4, 0),
-                                    (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE)])
+                                    (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE),
+                                    (T.KERNEL_PERSISTENT, 8, 2, 0, T.LAYOUT_PREFIX)])
 def test_in_voxel_binding_channels(config):
     spec = TissueSpec(3, 3, 6, seed=17).with_model(k_in=0.02, k_off=0.7)
     _run_both(spec, 0.2, 4, config=config)
 
 
 @pytest.mark.parametrize("config", [None, (T.KERNEL_WARP, 32, 4, 0),
-                                    (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE)])
+                                    (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE),
+                                    (T.KERNEL_PERSISTENT, 8, 4, 0, T.LAYOUT_PREFIX)])
 def test_medium_config_full_tissue(config):
     """64x64 cells of 16x16 voxels at dt = 0.1: the whole tissue, two steps,
     in the default launch shape (the benchmark's) and the warp kernel."""

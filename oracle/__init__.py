@@ -10,6 +10,10 @@ The C source (``tissue_oracle.c``) is compiled on first use into
 from .oracle import (  # noqa: F401
     Desc,
     Model,
+    Promoter,
+    ND,
+    PROMOTER,
+    E_STATE,
     EVENT_DTYPE,
     build,
     lib,

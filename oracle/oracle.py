@@ -25,6 +25,10 @@ _lib = None
 
 E_ARG = -1
 E_OVERFLOW = -4
+E_STATE = -9
+
+ND = 0        # Hill-repressed Delta-Notch lattice model
+PROMOTER = 1  # the paper's Notch model with one DNA promoter per cell (Sec. III-A1)
 
 
 class OracleError(RuntimeError):
@@ -57,8 +61,16 @@ _MODEL_FIELDS = ["kD", "K", "kN", "gD", "gN", "gR", "hopD", "hopN", "hopR",
                  "k_in", "k_off", "k_bind"]
 
 
+_PROMOTER_FIELDS = ["tD", "ka", "kd", "kN", "d", "hop"]
+
+
+class _Promoter(C.Structure):
+    _fields_ = [(f, C.c_double) for f in _PROMOTER_FIELDS]
+
+
 class _Model(C.Structure):
-    _fields_ = [(f, C.c_double) for f in _MODEL_FIELDS]
+    _fields_ = ([(f, C.c_double) for f in _MODEL_FIELDS] +
+                [("kind", C.c_int32), ("reserved", C.c_int32), ("pm", _Promoter)])
 
 
 EVENT_DTYPE = np.dtype([("step", "<u4"), ("kind", "<u4"), ("unit", "<u4"), ("e", "<u4"),
@@ -118,6 +130,28 @@ class Model:
         m = _Model()
         for f in _MODEL_FIELDS:
             setattr(m, f, float(getattr(self, f)))
+        m.kind = ND
+        return m
+
+
+@dataclass
+class Promoter:
+    """The promoter model's rates in lattice units (per unit time):
+    transcription tD, NICD binding ka (per NICD in the promoter's voxel),
+    unbinding kd, Delta -> NICD across a face kN, decay d, hop per direction."""
+    tD: float = 100.0
+    ka: float = 256.0
+    kd: float = 25.0
+    kN: float = 1.0
+    d: float = 1.0
+    hop: float = 256.0
+
+    def to_c(self) -> _Model:
+        m = _Model()
+        m.K = 1.0  # unused by this model
+        m.kind = PROMOTER
+        for f in _PROMOTER_FIELDS:
+            setattr(m.pm, f, float(getattr(self, f)))
         return m
 
 

@@ -15,8 +15,9 @@
  *      multiplies integers, so every sum is exact and order-free.
  *   4. Selection: r = floor(R64 * A / 2^64); the event is the first
  *      (voxel, channel) in canonical order whose running sum exceeds r.
- * Where the paper leaves the single-cell model open, the Notch-Delta lattice
- * model of the tissue workloads is used (Hill-repressed Delta production).
+ * Two single-cell models: the Notch-Delta lattice model of the tissue
+ * workloads (Hill-repressed Delta production), and the paper's own Notch
+ * model with one DNA promoter per cell (Sec. III-A1, Table I).
  */
 #include "tissue_oracle.h"
 
@@ -149,8 +150,10 @@ int orc_quantize(double x, uint64_t* q) {
 }
 
 typedef struct {
+  int kind;
   uint64_t kN, gD, gN, gR, hopD, hopN, hopR, k_in, k_off, k_bind;
   double kD, K;
+  uint64_t tD, ka, kd, kNc, d, hop;  /* promoter model (kNc: the face's k_N) */
 } qmodel;
 
 int orc_validate(const orc_desc* d, const orc_model* m) {
@@ -162,11 +165,19 @@ int orc_validate(const orc_desc* d, const orc_model* m) {
       if (!(d->init_lambda[s] >= 0.0 && d->init_lambda[s] <= 700.0)) return ORC_E_ARG;
   }
   if (m) {
-    const double r[12] = {m->kD, m->K, m->kN, m->gD, m->gN, m->gR,
-                          m->hopD, m->hopN, m->hopR, m->k_in, m->k_off, m->k_bind};
-    for (int i = 0; i < 12; ++i)
-      if (!rate_ok(r[i])) return ORC_E_ARG;
-    if (!(m->K > 0.0)) return ORC_E_ARG;
+    if (m->kind == ORC_MODEL_ND) {
+      const double r[12] = {m->kD, m->K, m->kN, m->gD, m->gN, m->gR,
+                            m->hopD, m->hopN, m->hopR, m->k_in, m->k_off, m->k_bind};
+      for (int i = 0; i < 12; ++i)
+        if (!rate_ok(r[i])) return ORC_E_ARG;
+      if (!(m->K > 0.0)) return ORC_E_ARG;
+    } else if (m->kind == ORC_MODEL_PROMOTER) {
+      const double r[6] = {m->pm.tD, m->pm.ka, m->pm.kd, m->pm.kN, m->pm.d, m->pm.hop};
+      for (int i = 0; i < 6; ++i)
+        if (!rate_ok(r[i])) return ORC_E_ARG;
+    } else {
+      return ORC_E_ARG;
+    }
   }
   return ORC_OK;
 }
@@ -174,6 +185,17 @@ int orc_validate(const orc_desc* d, const orc_model* m) {
 static int make_qmodel(const orc_model* m, qmodel* q) {
   int rc = orc_validate(NULL, m);
   if (rc) return rc;
+  memset(q, 0, sizeof(*q));
+  q->kind = m->kind;
+  if (m->kind == ORC_MODEL_PROMOTER) {
+    orc_quantize(m->pm.tD, &q->tD);
+    orc_quantize(m->pm.ka, &q->ka);
+    orc_quantize(m->pm.kd, &q->kd);
+    orc_quantize(m->pm.kN, &q->kNc);
+    orc_quantize(m->pm.d, &q->d);
+    orc_quantize(m->pm.hop, &q->hop);
+    return ORC_OK;
+  }
   orc_quantize(m->kN, &q->kN);
   orc_quantize(m->gD, &q->gD);
   orc_quantize(m->gN, &q->gN);
@@ -218,17 +240,44 @@ static int neighbour(int n, int v, int dir) {
   }
 }
 
-/* The 19 channels of voxel v, in canonical order:
+/* The voxel of a cell that holds its promoter: (n/2, n/2). */
+static int centre_voxel(int n) {
+  if (g_mutation == 9) return (n / 2 - 1) * n + n / 2;
+  return (n / 2) * n + n / 2;
+}
+
+/* The 19 channel slots of voxel v, in canonical order.
+ * Notch-Delta model:
  *   0 Delta production (Hill)      1 Notch production
  *   2..4 decay of D, N, R
  *   5..8 hop of D toward -x,+x,-y,+y   9..12 hop of N   13..16 hop of R
  *   17 D + N -> R (in-voxel)       18 R -> D + N
+ * Promoter model (R = bound sites, F = free sites):
+ *   0 transcription F -> F + D     1 unbinding R -> N + F
+ *   2, 3 decay of D, N             4 (none: DNA does not decay)
+ *   5..8 hop of D   9..12 hop of N   13..16 (none: DNA does not move)
+ *   17 binding N + F -> R          18 (none)
  * Values are exact (128-bit) so the overflow rule can be applied exactly. */
 static void voxel_channels(const qmodel* q, const int32_t* cell, int n, int v, u128 c[ORC_NCH]) {
   const int V = n * n;
   const uint64_t D = (uint64_t)cell[ORC_D * V + v];
   const uint64_t N = (uint64_t)cell[ORC_N * V + v];
   const uint64_t R = (uint64_t)cell[ORC_R * V + v];
+  if (q->kind == ORC_MODEL_PROMOTER) {
+    const uint64_t F = (uint64_t)(v == centre_voxel(n)) - R;  /* R <= sites, checked */
+    for (int j = 0; j < ORC_NCH; ++j) c[j] = 0;
+    c[0] = (u128)q->tD * F;
+    c[1] = (u128)q->kd * R;
+    c[2] = (u128)q->d * D;
+    c[3] = (u128)q->d * N;
+    for (int dir = 0; dir < 4; ++dir) {
+      int has = neighbour(n, v, dir) >= 0;
+      c[5 + dir] = has ? (u128)q->hop * D : 0;
+      c[9 + dir] = has ? (u128)q->hop * N : 0;
+    }
+    c[17] = (u128)q->ka * (N * F);
+    return;
+  }
   c[0] = hill_q(q, (int64_t)R);
   c[1] = q->kN;
   c[2] = (u128)q->gD * D;
@@ -333,11 +382,14 @@ static int chi_cell_q(const orc_desc* d, const qmodel* q, int32_t* counts, uint3
   int32_t* cell = counts + (size_t)c * 3 * V;
   uint64_t* a = (uint64_t*)malloc(sizeof(uint64_t) * V);
   if (!a) return ORC_E_ARG;
-  int ovf = 0;
-  for (int v = 0; v < V; ++v) a[v] = voxel_total(q, cell, n, v, &ovf);
+  int ovf = 0, bad_state = 0;
+  if (q->kind == ORC_MODEL_PROMOTER) /* bound sites never exceed the voxel's sites */
+    for (int v = 0; v < V; ++v)
+      if (cell[ORC_R * V + v] > (v == centre_voxel(n))) bad_state = 1;
+  for (int v = 0; v < V && !bad_state; ++v) a[v] = voxel_total(q, cell, n, v, &ovf);
   double t = 0.0;
   uint32_t e = 0;
-  int rc = ovf ? ORC_E_OVERFLOW : ORC_OK;
+  int rc = bad_state ? ORC_E_STATE : ovf ? ORC_E_OVERFLOW : ORC_OK;
   while (rc == ORC_OK) {
     uint64_t A = 0;
     for (int v = 0; v < V; ++v) A += a[v];
@@ -364,7 +416,12 @@ static int chi_cell_q(const orc_desc* d, const qmodel* q, int32_t* counts, uint3
     int32_t* Nv = &cell[ORC_N * V + v];
     int32_t* Rv = &cell[ORC_R * V + v];
     int u = -1;
-    switch (j) {
+    if (q->kind == ORC_MODEL_PROMOTER && (j == 1 || j == 17)) {
+      if (j == 1) /* unbinding releases the NICD into the promoter's voxel */
+        rc = (g_mutation == 8 ? 0 : bump(Nv, +1)) | bump(Rv, -1);
+      else        /* binding takes one NICD and occupies the site */
+        rc = bump(Nv, -1) | bump(Rv, +1);
+    } else switch (j) {
       case 0: rc = bump(Dv, +1); break;
       case 1: rc = bump(Nv, +1); break;
       case 2: rc = bump(Dv, -1); break;
@@ -441,8 +498,14 @@ static int sig_face_q(const orc_desc* d, const qmodel* q, int32_t* counts, uint3
     for (int p = 0; p < n && rc == ORC_OK; ++p) {
       int va, vb;
       face_voxels(n, axis, p, &va, &vb);
-      u128 x0 = (u128)q->k_bind * ((uint64_t)ca[ORC_D * V + va] * (uint64_t)cb[ORC_N * V + vb]);
-      u128 x1 = (u128)q->k_bind * ((uint64_t)cb[ORC_D * V + vb] * (uint64_t)ca[ORC_N * V + va]);
+      u128 x0, x1;
+      if (q->kind == ORC_MODEL_PROMOTER) { /* Delta(a) -> NICD(b), Delta(b) -> NICD(a) */
+        x0 = (u128)q->kNc * (uint64_t)ca[ORC_D * V + va];
+        x1 = (u128)q->kNc * (uint64_t)cb[ORC_D * V + vb];
+      } else {                             /* D(a) + N(b) -> R(b), D(b) + N(a) -> R(a) */
+        x0 = (u128)q->k_bind * ((uint64_t)ca[ORC_D * V + va] * (uint64_t)cb[ORC_N * V + vb]);
+        x1 = (u128)q->k_bind * ((uint64_t)cb[ORC_D * V + vb] * (uint64_t)ca[ORC_N * V + va]);
+      }
       if (x0 >= (u128)ORC_PROP_LIMIT || x1 >= (u128)ORC_PROP_LIMIT) rc = ORC_E_OVERFLOW;
       a[2 * p] = (uint64_t)x0;
       a[2 * p + 1] = (uint64_t)x1;
@@ -467,10 +530,17 @@ static int sig_face_q(const orc_desc* d, const qmodel* q, int32_t* counts, uint3
     int32_t* donor = dirn == 0 ? ca : cb;       /* cell giving Delta */
     int32_t* recv = dirn == 0 ? cb : ca;        /* cell giving Notch, receiving R */
     const int vd = dirn == 0 ? va : vb, vr = dirn == 0 ? vb : va;
-    int32_t* rcell = (g_mutation == 2) ? donor : recv;
-    const int vR = (g_mutation == 2) ? vd : vr;
-    rc = bump(&donor[ORC_D * V + vd], -1) | bump(&recv[ORC_N * V + vr], -1) |
-         bump(&rcell[ORC_R * V + vR], +1);
+    if (q->kind == ORC_MODEL_PROMOTER) {
+      /* the Delta leaves the donor; NICD appears in the facing voxel */
+      int32_t* ncell = (g_mutation == 10) ? donor : recv;
+      const int vN = (g_mutation == 10) ? vd : vr;
+      rc = bump(&donor[ORC_D * V + vd], -1) | bump(&ncell[ORC_N * V + vN], +1);
+    } else {
+      int32_t* rcell = (g_mutation == 2) ? donor : recv;
+      const int vR = (g_mutation == 2) ? vd : vr;
+      rc = bump(&donor[ORC_D * V + vd], -1) | bump(&recv[ORC_N * V + vr], -1) |
+           bump(&rcell[ORC_R * V + vR], +1);
+    }
     if (rc) { rc = ORC_E_OVERFLOW; break; }
     e += 1;
     if (e == 0xFFFFFFFFu) { rc = ORC_E_OVERFLOW; break; }
@@ -582,7 +652,7 @@ static int step_impl(const orc_desc* d, const orc_model* m, int32_t* counts, uin
       if (!err) err |= face_phase(d, &q, counts, 0, ORC_TAG_SX2, k, half, last, n_events, t_last,
                                   n_threads, trace, cap, len);
     }
-    if (err) rc = ORC_E_OVERFLOW;
+    if (err) rc = (err & -ORC_E_STATE) == -ORC_E_STATE ? ORC_E_STATE : ORC_E_OVERFLOW;
   }
   return rc;
 }

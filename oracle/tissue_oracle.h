@@ -37,6 +37,7 @@ extern "C" {
 #define ORC_OK 0
 #define ORC_E_ARG (-1)
 #define ORC_E_OVERFLOW (-4)
+#define ORC_E_STATE (-9)   /* a promoter-model state with more bound sites than sites */
 
 /* Philox counter word 3 carries the tissue id in its low 24 bits and a tag
  * naming the stream in its high 8 bits. */
@@ -64,8 +65,32 @@ typedef struct {
   double init_lambda[3];    /* Poisson mean of the initial count of D, N, R per voxel */
 } orc_desc;
 
+/* The paper's own Notch model (Sec. III-A1, Table I) on the voxel lattice.
+ * One DNA promoter site per cell, at the centre voxel (n/2, n/2).  Species
+ * slots: D = Delta, N = NICD, R = bound promoter sites (0 or 1 at the centre
+ * voxel, 0 elsewhere); the free sites of voxel v are F_v = [v is the centre]
+ * - R_v.  Within a cell:
+ *   free promoter transcribes Delta        F -> F + D      t_D * F
+ *   NICD binds the free promoter           N + F -> R      k_a * N * F
+ *   NICD unbinds                           R -> N + F      k_d * R
+ *   Delta and NICD degrade (DNA does not)  D -> 0, N -> 0  d * D, d * N
+ *   Delta and NICD hop to each existing neighbour voxel at `hop` each.
+ * Across a face (the signalling module): each Delta in a face voxel turns
+ * into NICD in the facing voxel of the other cell at k_N per molecule.
+ * Rates are per unit time, already in lattice units (hop = diffusion
+ * constant / h^2, k_a = bimolecular constant / voxel volume). */
+typedef struct {
+  double tD, ka, kd, kN, d, hop;
+} orc_promoter;
+
+#define ORC_MODEL_ND 0        /* Hill-repressed Delta-Notch lattice model (the rates below) */
+#define ORC_MODEL_PROMOTER 1  /* the paper's promoter model (pm below) */
+
 typedef struct {
   double kD, K, kN, gD, gN, gR, hopD, hopN, hopR, k_in, k_off, k_bind;
+  int32_t kind;             /* ORC_MODEL_ND or ORC_MODEL_PROMOTER */
+  int32_t reserved;
+  orc_promoter pm;          /* used when kind == ORC_MODEL_PROMOTER */
 } orc_model;
 
 /* One fired event, for full-trace comparisons on small cases. */
@@ -76,7 +101,7 @@ typedef struct {
   uint32_t e;        /* event index within this module call */
   double t;          /* local time of the event in [0, dt) */
   uint32_t site;     /* voxel (chi) or voxel pair p (S) */
-  uint32_t channel;  /* channel index 0..18 (chi) or 0/1 within the pair (S) */
+  uint32_t channel;  /* channel slot 0..18 (chi) or 0/1 within the pair (S) */
 } orc_event;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

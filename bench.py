@@ -48,9 +48,9 @@ ISSUE_PEAK_GINST = 152 * 4 * 2.070
 # Warp instructions the chi kernel executes per chi event on the medium
 # tissue, per launch variant, from ncu (smsp__inst_executed.sum over the 10
 # timed chi launches / their chi events; profiles/k_chi_medium_metrics.md).
-CHI_INST_PER_EVENT = {("persistent", 16, 0): 325.8}
+CHI_INST_PER_EVENT = {("persistent", 16, 0): 327.3}
 # DRAM bytes (read + write) per chi launch from the same capture, per variant.
-CHI_TRAFFIC = {("persistent", 16, 0): 1.312e7}
+CHI_TRAFFIC = {("persistent", 16, 0): 1.321e7}
 # Algorithmic DRAM bytes of one chi launch per cell: the state read + write.
 STATE_BYTES_PER_CELL_RW = lambda V: 2 * 3 * V * 4  # noqa: E731
 
@@ -269,6 +269,8 @@ def run_ours(args, rank, world, local_rank):
         "wall_s_timed": wall,
     }
     g.close()
+    if rank == 0 and not args.no_promoter:
+        out["promoter"] = promoter_leg(args)
     if rank == 0 and not args.no_batch:
         out["batched"] = batch_leg(args)
     if rank == 0 and args.serving:
@@ -279,6 +281,51 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+def promoter_leg(args) -> dict:
+    """The paper's promoter Notch model (Table I rates in lattice units) on a
+    64x64 tissue of 16x16-voxel cells, dt = 0.1 s, after 2 s of burn-in:
+    the same timing as the main line (device-resident state, L2 flushed
+    between timed steps, CUDA events on the tissue's stream)."""
+    import torch
+
+    from paper_1806_10889_gb300.tissue import Tissue
+
+    run = W.promoter()
+    g = Tissue(run.tissue)
+    g.step(run.dt, 20)
+    g.step(run.dt, 3)
+    g.sync()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev0 = g.total_events()
+    total_ms = chi_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c_ms, _ = g.step_timed(run.dt, 1)
+        b.record(stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+        chi_ms += c_ms
+    ev = g.total_events() - ev0
+    launch = g.launch_config()
+    g.close()
+    spec = run.tissue
+    return {"workload": f"promoter model, {spec.width}x{spec.height} cells of {spec.n}x{spec.n} "
+                        "voxels, dt 0.1 s, burn-in 2 s",
+            "rates": {k: v for k, v in spec.model.items() if k != "kind"},
+            "events_per_s": float(ev.sum()) / (total_ms / 1e3),
+            "chi_events_per_s": float(ev[0]) / (chi_ms / 1e3),
+            "cell_steps_per_s": spec.cells * args.steps / (total_ms / 1e3),
+            "events_per_step": float(ev.sum()) / args.steps,
+            "face_events_per_step": float(ev[1] + ev[2]) / args.steps,
+            "ms_per_step": total_ms / args.steps, "chi_ms_per_step": chi_ms / args.steps,
+            "chi_launch": {"kernel": ["warp", "persistent"][launch[0]],
+                           "lanes_per_cell": launch[1], "warps_per_block": launch[2]}}
 
 
 def batch_leg(args) -> dict:
@@ -449,6 +496,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain leg")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--no-promoter", action="store_true", help="skip the promoter-model leg")
     ap.add_argument("--serving", type=int, default=0, help="serve the first K requests")
     ap.add_argument("--serving-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

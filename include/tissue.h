@@ -14,7 +14,9 @@
  *   (the "-seed" of the module command lines, Fig. 3).
  *
  *   chi here is a lattice RDME on an n x n voxel grid solved by the exact
- *   direct-method SSA; S is Delta-Notch binding across a shared face, with
+ *   direct-method SSA, with one of two single-cell models (tissue_model, or
+ *   the paper's promoter model, tissue_promoter_model); S is the Delta-Notch
+ *   reaction across a shared face, with
  *   every boundary voxel coupled to a single face (Sec. III-A1), realised as
  *   an x-face phase followed by a y-face phase.
  *
@@ -59,6 +61,7 @@ extern "C" {
 #define TISSUE_E_CUDA (-5)     /* a CUDA runtime call failed */
 #define TISSUE_E_TIMEOUT (-6)  /* a bounded device wait gave up */
 #define TISSUE_E_BUDGET (-7)   /* admission refused: memory budget exceeded */
+#define TISSUE_E_STATE (-9)    /* promoter model: a voxel holds more bound sites than sites */
 
 #define TISSUE_COUNT_MAX ((1 << 30) - 1)
 
@@ -83,6 +86,24 @@ typedef struct {
   double kD, K, kN, gD, gN, gR, hopD, hopN, hopR, k_in, k_off, k_bind;
 } tissue_model;
 
+/* The paper's own Notch model (arXiv 1806.10889, Sec. III-A1, Table I) on the
+ * voxel lattice.  Each cell holds one DNA promoter site at voxel (n/2, n/2).
+ * The species slots are read as D = Delta, N = NICD, and R = bound promoter
+ * sites (0 or 1 at the promoter voxel, 0 elsewhere).  A voxel's free sites
+ * are F = [v is the promoter voxel] - R.  Per voxel:
+ *   transcription F -> F + D at tD*F; NICD binding N + F -> R at ka*N*F;
+ *   unbinding R -> N + F at kd*R; decay of D and N at d each (DNA does not
+ *   decay); hop of each Delta and NICD to each existing neighbour voxel at hop.
+ * Across a face, for every voxel pair (i in one cell, j facing it in the other):
+ *   Delta(i) -> NICD(j) at kN*D(i), in both directions.
+ * Rates are per unit time in lattice units (all finite, >= 0 and < 2^20).
+ * A state may not hold more bound sites than sites; if it does, the next
+ * step's chi leaves that cell unchanged and latches TISSUE_E_STATE.  Initial
+ * counts with init_lambda[2] = 0 start with every promoter free. */
+typedef struct {
+  double tD, ka, kd, kN, d, hop;
+} tissue_promoter_model;
+
 /* Bytes of the caller-owned state buffer: width*height*3*n*n*4.
  * Returns 0 for an invalid descriptor. */
 size_t tissue_state_bytes(const tissue_desc* desc);
@@ -101,6 +122,12 @@ int tissue_create(const tissue_desc* desc, void* dev_counts, size_t bytes, void*
 
 /* Set (or replace, between steps) the model; the rates are copied. */
 int tissue_set_model(tissue* t, const tissue_model* model);
+
+/* Set (or replace, between steps) the promoter model instead; the rates are
+ * copied.  A promoter-model tissue steps with the persistent chi kernel only:
+ * tissue_step returns TISSUE_E_ARG while the launch configuration selects
+ * TISSUE_KERNEL_WARP, and tissue_step_noalloc does not take it. */
+int tissue_set_promoter_model(tissue* t, const tissue_promoter_model* model);
 
 /* Overwrite the state from host memory (n int32 values, exactly
  * width*height*3*V) and set the global step index (checkpoint resume).
@@ -181,7 +208,7 @@ int tissue_get_launch_config(const tissue* t, tissue_launch* config);
  * replayed.  Each tissue's trajectory is bit-identical to stepping it alone.
  * While a batch exists, step its members only through it; a member's model
  * must not change (recreate the batch instead).  The members must outlive
- * the batch. */
+ * the batch.  Members of both models may share a batch and a chi launch. */
 typedef struct tissue_batch tissue_batch;
 
 /* count >= 1 distinct tissues with models set, on the current device.

@@ -1,0 +1,504 @@
+// K_chi, persistent segmented form: the intracellular module chi (arXiv
+// 1806.10889, Sec. II-A1) over a work list of cells, H lanes per cell.
+//
+// A warp is split into 32/H segments (H = 32, 16 or 8); each segment runs one
+// cell's direct-method SSA exactly as the one-warp-per-cell kernel does
+// (same Philox stream, same integer propensities, same binary64 clock), so
+// both kernels give identical results.  With H < 32 every uniform
+// instruction of the event loop -- waiting time, selection arithmetic,
+// decoding -- serves several cells at once.  When a segment's cell reaches
+// the end of the step it writes the cell back and takes the next item from
+// the work list (one atomic add), so cells of different cost and tissues of
+// different size share one launch without idle warps.
+//
+// Per segment, shared memory holds a copy of its tissue's view (model,
+// pointers), the within-block prefix pre[] and the counts cnt[][] as in the
+// one-warp kernel.  Lane l of a segment owns voxels l*B .. l*B+B-1 (B a power
+// of two, H*B >= V).  The channel of the selected voxel is found without a
+// scan: lane j evaluates the running sum C_j of channels 0..j in closed form
+// (hop channels enter through the count of existing neighbour directions);
+// with H = 16, C_16..C_18 follow from C_15 by three additions.
+//
+// Both single-cell models share the 19 channel slots.  Per voxel a model
+// contributes three terms -- c0 (slot 0), c1 (slot 1) and the bimolecular
+// product X of slot 17 -- and affine terms in D, N and R:
+//   Notch-Delta:  c0 = Hill(R), c1 = kN,        X = D N
+//   promoter:     c0 = t_D F,   c1 = k_d R,     X = N F
+// where F = [v is the promoter voxel] - R counts the free promoter sites
+// (the paper's Notch model, Sec. III-A1: R counts bound sites).
+//
+// Template parameters: H lanes per cell; PRE the shared-memory layout; QB
+// whether a lane may cover several voxels of a block (B > H, i.e. V > H^2);
+// GEN whether the launch may hold promoter-model tissues (false: Notch-Delta
+// only, with the model test folded away).  The launcher picks QB and GEN from
+// the largest cell and the models of the listed tissues.
+#pragma once
+#include "tissue_dev.cuh"
+
+namespace tsg {
+
+namespace {
+
+constexpr int kViewBytes = (static_cast<int>(sizeof(TissueView)) + 15) & ~15;
+static_assert(sizeof(TissueView) % 8 == 0, "view copy uses 8-byte words");
+
+struct Seg {
+  int V, n, B, lb;  // voxels, side, voxels per lane block, log2 B
+  uint32_t magic;
+  int qb;           // log2 of the voxels each lane covers inside one block (B > H)
+  int centre;       // the promoter voxel (n/2, n/2)
+};
+
+// The model terms c0, c1 and X of a voxel (see the file comment).
+template <bool GEN>
+__device__ __forceinline__ void voxel_terms(bool pm, const QRates& q, int v, const Seg& s,
+                                            uint32_t D, uint32_t N, uint32_t R, bool act,
+                                            uint64_t& c0, uint64_t& c1, uint64_t& X) {
+  if (GEN && pm) {
+    const uint32_t F = static_cast<uint32_t>(v == s.centre) - R;
+    c0 = q.tD * F;
+    c1 = q.kd * R;
+    X = static_cast<uint64_t>(N) * F;
+  } else {
+    c0 = act ? hill_q(q, R) : 0ull;  // no table read for an idle segment
+    c1 = q.kN;
+    X = static_cast<uint64_t>(D) * N;
+  }
+}
+
+// Existence mask of the four neighbour directions (-x, +x, -y, +y) of v.
+__device__ __forceinline__ uint32_t dir_mask(int v, const Seg& s) {
+  const int vy = div_n(v, s.magic), vx = v - vy * s.n;
+  return static_cast<uint32_t>(vx > 0) | (static_cast<uint32_t>(vx < s.n - 1) << 1) |
+         (static_cast<uint32_t>(vy > 0) << 2) | (static_cast<uint32_t>(vy < s.n - 1) << 3);
+}
+
+// Total propensity of voxel v (see voxel_total in k_chi.cu; same value).
+template <bool GEN>
+__device__ __forceinline__ uint64_t seg_voxel_total(const int32_t* cnt, int vmax, int v,
+                                                    const Seg& s, const QRates& q, bool pm,
+                                                    bool& ovf) {
+  const uint32_t D = static_cast<uint32_t>(cnt[v]);
+  const uint32_t N = static_cast<uint32_t>(cnt[vmax + v]);
+  const uint32_t R = static_cast<uint32_t>(cnt[2 * vmax + v]);
+  const int nn = __popc(dir_mask(v, s));
+  uint64_t c0, c1, X;
+  voxel_terms<GEN>(pm, q, v, s, D, N, R, true, c0, c1, X);
+  const uint64_t base = c0 + c1;
+  if ((D | N | R) < q.small) {
+    return base + q.cD[nn] * D + q.cN[nn] * N + q.cRo[nn] * R + q.k_in * X;
+  }
+  uint64_t a = base;
+  a += mul_lim(q.cD[nn], D, ovf);
+  a += mul_lim(q.cN[nn], N, ovf);
+  a += mul_lim(q.cR[nn], R, ovf);
+  a += mul_lim(q.k_in, X, ovf);
+  a += mul_lim(q.k_off, R, ovf);
+  ovf |= (a >> 52) != 0ull;
+  return a;
+}
+
+// Lane constants for the closed-form running sum C_j of channel j: which of
+// the first five channels are included, which hop directions of D, N and R.
+struct ChanLane {
+  uint32_t mD, mN, mR;   // direction masks counted in C_j
+  bool f1, f2, f3, f4, f17, f18, valid;
+};
+
+__device__ __forceinline__ ChanLane chan_lane(int j) {
+  ChanLane c;
+  c.valid = j < 19;
+  c.f1 = j >= 1;
+  c.f2 = j >= 2;
+  c.f3 = j >= 3;
+  c.f4 = j >= 4;
+  c.f17 = j >= 17;
+  c.f18 = j >= 18;
+  c.mD = j < 5 ? 0u : j <= 8 ? (2u << (j - 5)) - 1u : 0xFu;
+  c.mN = j < 9 ? 0u : j <= 12 ? (2u << (j - 9)) - 1u : 0xFu;
+  c.mR = j < 13 ? 0u : j <= 16 ? (2u << (j - 13)) - 1u : 0xFu;
+  return c;
+}
+
+// PRE selects the shared-memory layout: true keeps the within-block prefix
+// pre[] of the voxel propensities (20 B per voxel); false keeps only the
+// counts (12 B per voxel) and recomputes the selected block's propensities,
+// trading ~70 instructions per pass for ~40% more cells resident per SM.
+// Running sum C_j of the channels 0..j of a voxel (~0 for j >= 19).
+__device__ __forceinline__ uint64_t chan_cum(const ChanLane& c, const QRates& q, uint64_t c0,
+                                             uint64_t c1, uint32_t D, uint32_t N, uint32_t R,
+                                             uint64_t X, uint32_t hm) {
+  if (!c.valid) return ~0ull;
+  return c0 + (c.f1 ? c1 : 0ull) + D * ((c.f2 ? q.gD : 0ull) + q.hopD * __popc(hm & c.mD)) +
+         N * ((c.f3 ? q.gN : 0ull) + q.hopN * __popc(hm & c.mN)) +
+         R * ((c.f4 ? q.gR : 0ull) + q.hopR * __popc(hm & c.mR) + (c.f18 ? q.k_off : 0ull)) +
+         (c.f17 ? q.k_in * X : 0ull);
+}
+
+template <int H, bool PRE, bool QB, bool GEN>
+__global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
+                                                 const TissueView* __restrict__ views,
+                                                 const uint2* __restrict__ items,
+                                                 const uint32_t n_items, uint32_t* counter,
+                                                 const uint32_t seg_bytes,
+                                                 const uint32_t step_off, const double dt) {
+  constexpr int G = 32 / H;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int seg = lane / H, sl = lane % H;
+  constexpr unsigned kSegBits = H == 32 ? kFull : ((1u << H) - 1u);
+  const unsigned segmask = H == 32 ? kFull : (kSegBits << (H * seg));
+  unsigned char* base = smem + static_cast<size_t>(wib * G + seg) * seg_bytes;
+  TissueView* sv = reinterpret_cast<TissueView*>(base);
+  constexpr int kBytesPerVoxel = PRE ? 20 : 12;
+  const int vmax = static_cast<int>((seg_bytes - kViewBytes) / kBytesPerVoxel);
+  uint64_t* pre = reinterpret_cast<uint64_t*>(base + kViewBytes);  // used only if PRE
+  int32_t* cnt = reinterpret_cast<int32_t*>(base + kViewBytes + (PRE ? 8 * vmax : 0));
+  const ChanLane cl = chan_lane(sl);
+  const ChanLane cl2 = chan_lane(sl + H);  // second channel of each lane when H = 8
+
+  static_assert(PRE || !QB, "the recompute layout needs B <= H");
+  bool have = false, done = false, pm = false;
+  Seg s{0, 2, 1, 0, 1, 0, 0};
+  uint32_t cell = 0, step = 0, word3 = 0, key0 = 0, key1 = 0, e = 0, e0 = 0;
+  uint64_t A = 0, P = 0, Em = 0, Rb = 0, Em2 = 0, Rb2 = 0;
+  int Ek = -1, Ek2 = -1, err = 0;
+  bool next_ok = false;  // the draws of events e0+H+sl are in Em2/Ek2/Rb2
+  double tnow = 0.0;
+  int32_t* g = nullptr;
+
+  for (;;) {
+    // ---- a segment without a cell takes the next work item ----------------
+    if (!have && !done) {
+      uint32_t it = 0;
+      if (sl == 0) it = atomicAdd(counter, 1u);
+      it = __shfl_sync(segmask, it, 0, H);
+      if (it >= n_items) {
+        done = true;
+      } else {
+        const uint2 w = items ? items[it] : make_uint2(0u, it);
+        cell = w.y;
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(views + w.x);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(sv);
+        for (int i = sl; i < static_cast<int>(sizeof(TissueView) / 8); i += H) dst[i] = src[i];
+        __syncwarp(segmask);
+        s.V = static_cast<int>(sv->V);
+        s.n = static_cast<int>(sv->n);
+        s.magic = sv->magic;
+        s.lb = 0;
+        while ((H << s.lb) < s.V) ++s.lb;
+        s.B = 1 << s.lb;
+        s.qb = 0;
+        while ((H << s.qb) < s.B) ++s.qb;
+        s.centre = (s.n >> 1) * s.n + (s.n >> 1);
+        pm = GEN && sv->q.kind == kModelPromoter;
+        g = sv->counts + static_cast<size_t>(cell) * 3 * s.V;
+        if ((s.V & 3) == 0) {
+          const int V4 = s.V >> 2;
+          for (int sp = 0; sp < 3; ++sp) {
+            const int4* a = reinterpret_cast<const int4*>(g + sp * s.V);
+            int4* b = reinterpret_cast<int4*>(cnt + sp * vmax);
+            for (int i = sl; i < V4; i += H) b[i] = a[i];
+          }
+        } else {
+          for (int sp = 0; sp < 3; ++sp)
+            for (int i = sl; i < s.V; i += H) cnt[sp * vmax + i] = g[sp * s.V + i];
+        }
+        __syncwarp(segmask);
+        step = *sv->step + step_off;
+        key0 = static_cast<uint32_t>(sv->seed);
+        key1 = static_cast<uint32_t>(sv->seed >> 32);
+        word3 = sv->tissue_id | (kTagChi << 24);
+        bool ovf = false, bad_state = false;
+        const bool bad_qb = !QB && s.qb > 0;  // the launcher never lets this happen
+        uint64_t S = 0;
+        for (int i = 0; i < s.B; ++i) {
+          const int v = (sl << s.lb) + i;
+          if (v < s.V) {
+            // promoter model: bound sites never exceed the voxel's sites
+            if (pm && cnt[2 * vmax + v] > static_cast<int32_t>(v == s.centre)) bad_state = true;
+            S += seg_voxel_total<GEN>(cnt, vmax, v, s, sv->q, pm, ovf);
+            if (PRE) pre[v] = S;
+          }
+        }
+        P = S;
+#pragma unroll
+        for (int o = 1; o < H; o <<= 1) {
+          const uint64_t y = __shfl_up_sync(segmask, P, o, H);
+          if (sl >= o) P += y;
+        }
+        A = __shfl_sync(segmask, P, H - 1, H);
+        tnow = 0.0;
+        e = 0;
+        e0 = 0;
+        draw_event(e0 + sl, step, cell, word3, key0, key1, Em, Ek, Rb);
+        next_ok = false;
+        err = bad_qb                         ? kErrInternal
+              : __any_sync(segmask, bad_state) ? kErrState
+              : __any_sync(segmask, ovf)       ? kErrOverflow
+                                               : 0;
+        have = true;
+        __syncwarp(segmask);
+      }
+    }
+    if (__all_sync(kFull, done)) break;
+
+    // ---- one event of every active segment (the whole warp in step) -------
+    const bool act = have;
+    const int qb = QB ? s.qb : 0;  // log2 of the voxels a lane covers in the selected block
+    int j = static_cast<int>(e - e0);
+    // Draws come in batches of H events per segment.  A segment that has used
+    // its batch takes the prepared next one if it has it; when some segment
+    // has none, every segment without a prepared batch draws in the same
+    // pass, so the segments of a warp share the Philox / -ln work.
+    bool must = false;
+    if (act && j == H) {
+      if (next_ok) {
+        Em = Em2;
+        Ek = Ek2;
+        Rb = Rb2;
+        next_ok = false;
+        e0 += H;
+        j = 0;
+      } else {
+        must = true;
+      }
+    }
+    if (__any_sync(kFull, must)) {
+      if (must || (act && !next_ok)) {
+        const uint32_t base = e0 + H;  // the batch after the one in use
+        uint64_t m_, r_;
+        int k_;
+        draw_event(base + sl, step, cell, word3, key0, key1, m_, k_, r_);
+        if (must) {
+          Em = m_;
+          Ek = k_;
+          Rb = r_;
+          e0 += H;
+          j = 0;
+        } else {
+          Em2 = m_;
+          Ek2 = k_;
+          Rb2 = r_;
+          next_ok = true;
+        }
+      }
+    }
+    const uint64_t mE = __shfl_sync(kFull, Em, j, H);
+    const int kE = __shfl_sync(kFull, Ek, j, H);
+    const uint64_t R64 = __shfl_sync(kFull, Rb, j, H);
+    const uint64_t Aa = act ? A : 0ull;
+    const double tn = __dadd_rn(tnow, tau_from(F53{mE, kE}, kE < 0 || Aa == 0ull, Aa | (Aa == 0ull)));
+
+    const uint64_t r = __umul64hi(R64, Aa);
+    const unsigned m1 = (__ballot_sync(kFull, r < P && act) >> (seg * H)) & kSegBits;
+    const int L = m1 ? __ffs(m1) - 1 : 0;
+    const uint64_t Pl = __shfl_sync(kFull, P, L > 0 ? L - 1 : 0, H);
+    const uint64_t r1 = r - (L > 0 ? Pl : 0ull);
+    const int vb = L << s.lb;
+    const QRates& q = sv->q;
+    uint64_t pv = ~0ull;
+    if (PRE) {
+      // lane sl covers voxels vb + sl*Q .. + Q-1 of the block (Q = 2^qb; 1 if B <= H)
+      const int q0 = vb + (sl << qb);
+      if ((sl << qb) < s.B && q0 < s.V) pv = pre[min(q0 + (1 << qb) - 1, s.V - 1)];
+    } else {
+      // the block's voxel propensities, recomputed, then their running sum
+      bool unused = false;
+      const bool mine = act && sl < s.B && vb + sl < s.V;
+      uint64_t cx = mine ? seg_voxel_total<GEN>(cnt, vmax, vb + sl, s, q, pm, unused) : 0ull;
+#pragma unroll
+      for (int o = 1; o < H; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(kFull, cx, o, H);
+        if (sl >= o) cx += y;
+      }
+      if (sl < s.B && vb + sl < s.V) pv = cx;
+    }
+    const unsigned m2 = (__ballot_sync(kFull, r1 < pv) >> (seg * H)) & kSegBits;
+    const int i2 = m2 ? __ffs(m2) - 1 : 0;
+    const uint64_t pp = __shfl_sync(kFull, pv, i2 > 0 ? i2 - 1 : 0, H);
+    uint64_t r2 = r1 - (i2 > 0 ? pp : 0ull);
+    int v = vb + (i2 << qb);
+    bool bad_q = false;
+    if (PRE && QB && qb > 0) {
+      // the voxel inside lane i2's run of Q voxels: a short uniform scan
+      uint64_t before_v = i2 > 0 ? pp : 0ull;
+      int pick = -1;
+      for (int kq = 0; kq < (1 << qb); ++kq) {
+        const int idx = v + kq;
+        if (pick < 0 && idx < s.V) {
+          const uint64_t x = pre[idx];
+          if (r1 < x) {
+            pick = idx;
+            r2 = r1 - before_v;
+          }
+          before_v = x;
+        }
+      }
+      bad_q = pick < 0;
+      v = pick < 0 ? v : pick;
+    }
+    const bool bad1 = act && Aa != 0ull &&
+                      (m1 == 0u || m2 == 0u || (i2 << qb) >= s.B || v >= s.V || bad_q);
+    if (bad1 || v >= s.V) v = 0;
+
+    // channel: closed-form running sums
+    const uint32_t D = static_cast<uint32_t>(cnt[v]);
+    const uint32_t N = static_cast<uint32_t>(cnt[vmax + v]);
+    const uint32_t R = static_cast<uint32_t>(cnt[2 * vmax + v]);
+    const uint32_t hm = dir_mask(v, s);
+    uint64_t c0, c1, X;
+    voxel_terms<GEN>(pm, q, v, s, D, N, R, act, c0, c1, X);
+    const uint64_t C = chan_cum(cl, q, c0, c1, D, N, R, X, hm);
+    const uint64_t Cb = H == 8 ? chan_cum(cl2, q, c0, c1, D, N, R, X, hm) : ~0ull;
+    uint64_t C16 = 0, C17 = 0, C18;
+    if (H <= 16) {
+      // C_16..C_18 from C_15: +x hop of R (if that neighbour exists), slots 17, 18
+      const uint64_t C15 = __shfl_sync(kFull, H == 16 ? C : Cb, H == 16 ? 15 : 7, H);
+      C16 = C15 + (((hm >> 3) & 1u) ? q.hopR * R : 0ull);
+      C17 = C16 + q.k_in * X;
+      C18 = C17 + q.k_off * R;
+    } else {
+      C18 = __shfl_sync(kFull, C, 18, H);
+    }
+    const unsigned m3 = (__ballot_sync(kFull, r2 < C) >> (seg * H)) & kSegBits;
+    const unsigned m3b = H == 8 ? (__ballot_sync(kFull, r2 < Cb) >> (seg * H)) & kSegBits : 0u;
+    int ch = m3 ? __ffs(m3) - 1
+                : m3b ? H + __ffs(m3b) - 1
+                      : 16 + static_cast<int>(r2 >= C16) + static_cast<int>(r2 >= C17);
+    const bool bad = bad1 || (act && Aa != 0ull && !(r2 < C18));
+    const uint64_t a_old_v = C18;
+    if (ch > 18) ch = 18;
+
+    const bool fire = act && err == 0 && !bad && Aa != 0ull && before(tn, dt);
+    // the channel's effect, decoded without branches
+    const bool hop = ch >= 5 && ch <= 16;
+    const int hs = (ch - 5) >> 2, hd = (ch - 5) & 3;
+    int u = hop ? v + (hd == 0 ? -1 : hd == 1 ? 1 : hd == 2 ? -s.n : s.n) : -1;
+    const bool bad_u = fire && hop && (u < 0 || u >= s.V);
+    if (u >= s.V) u = -1;
+    const bool fire_ok = fire && !bad_u;
+    uint64_t a_old_u = 0;
+    if (PRE && u >= 0) a_old_u = pre[u] - ((u & (s.B - 1)) ? pre[u - 1] : 0ull);
+    __syncwarp();
+    if (fire_ok && sl < 3) {
+      // Notch-Delta: slot 17 is D + N -> R, 18 is R -> D + N.  Promoter:
+      // slot 1 (unbinding) also frees the site (R - 1), slot 17 (binding) is
+      // N + F -> R, and slots 4, 13..16 and 18 have no propensity.
+      const bool pm1 = GEN && pm && ch == 1, pm17 = GEN && pm && ch == 17;
+      int sp, dd, xv = v;
+      if (sl == 0) {
+        sp = ch <= 1 ? ch : ch <= 4 ? ch - 2 : hop ? hs : ch == 17 ? (pm17 ? 1 : 0) : 2;
+        dd = ch <= 1 ? 1 : -1;
+      } else if (sl == 1) {
+        sp = hop ? hs : ch == 17 ? 1 : 0;
+        dd = hop ? 1 : ch == 17 ? (pm17 ? 0 : -1) : ch == 18 ? 1 : 0;
+        if (hop) xv = u;
+      } else {
+        sp = (ch == 17 || pm1) ? 2 : 1;
+        dd = ch >= 17 ? 1 : pm1 ? -1 : 0;
+      }
+      if (dd != 0) {
+        int32_t* c = &cnt[sp * vmax + xv];
+        const int nv = *c + dd;
+        *c = nv;
+        if (nv > kCountMax) err |= kErrOverflow;
+      }
+    }
+    __syncwarp();
+    bool ovf = false;
+    uint64_t dv, du;
+    if (PRE) {
+      const uint64_t a_new =
+          act ? seg_voxel_total<GEN>(cnt, vmax, (sl == 1 && u >= 0) ? u : v, s, q, pm, ovf)
+              : 0ull;
+      dv = __shfl_sync(kFull, a_new, 0, H) - a_old_v;
+      du = __shfl_sync(kFull, a_new, 1, H) - a_old_u;
+    } else {
+      dv = (act ? seg_voxel_total<GEN>(cnt, vmax, v, s, q, pm, ovf) : 0ull) - a_old_v;
+      // one molecule of species hs arrived at u: the change of u's total in
+      // closed form (the total is affine in D and N apart from k_in X)
+      du = 0;
+      if (act && u >= 0) {
+        const uint32_t Du = static_cast<uint32_t>(cnt[u]);
+        const uint32_t Nu = static_cast<uint32_t>(cnt[vmax + u]);
+        const uint32_t Ru = static_cast<uint32_t>(cnt[2 * vmax + u]);
+        const int nnu = __popc(dir_mask(u, s));
+        if (GEN && pm) {  // X = N F: a Delta adds cD, a NICD adds cN + k_a F (R never hops)
+          const uint32_t Fu = static_cast<uint32_t>(u == s.centre) - Ru;
+          du = hs == 0 ? q.cD[nnu] : q.cN[nnu] + q.k_in * Fu;
+        } else if (hs == 0) {
+          du = q.cD[nnu] + q.k_in * Nu;
+        } else if (hs == 1) {
+          du = q.cN[nnu] + q.k_in * Du;
+        } else {
+          du = q.cRo[nnu] + (hill_q(q, Ru) - hill_q(q, Ru - 1u));
+        }
+        if (((Du | Nu | Ru) >= q.small) && fire_ok) {
+          bool o2 = false;  // large counts: check the new total exactly
+          seg_voxel_total<GEN>(cnt, vmax, u, s, q, pm, o2);
+          ovf |= o2;
+        }
+      }
+    }
+    if (fire_ok) {
+      const int bv = v >> s.lb;
+      P += sl >= bv ? dv : 0ull;
+      A += dv;
+      if (u >= 0) {
+        const int bu = u >> s.lb;
+        P += sl >= bu ? du : 0ull;
+        A += du;
+      }
+      if (PRE && (sl << qb) < s.B) {
+        // prefix entries from the changed voxel to the end of its block
+        for (int kq = 0; kq < (1 << qb); ++kq) {
+          const int off = (sl << qb) + kq;  // position inside the block
+          const int iv = (bv << s.lb) + off;
+          if (off >= (v & (s.B - 1)) && iv < s.V) pre[iv] += dv;
+          if (u >= 0) {
+            const int iu = ((u >> s.lb) << s.lb) + off;
+            if (off >= (u & (s.B - 1)) && iu < s.V) pre[iu] += du;
+          }
+        }
+      }
+      tnow = tn;
+      ++e;
+      if (e == 0xFFFFFFFFu) err |= kErrEventIndex;
+      if (ovf) err |= kErrOverflow;
+    }
+    if (bad || bad_u) err |= kErrInternal;
+    __syncwarp();
+
+    // ---- a segment whose cell is finished writes it back ------------------
+    const unsigned seg_err = (__ballot_sync(kFull, err != 0) >> (seg * H)) & kSegBits;
+    const bool finish = act && (!fire_ok || seg_err != 0u);
+    if (finish) {
+      if ((s.V & 3) == 0) {
+        const int V4 = s.V >> 2;
+        for (int sp = 0; sp < 3; ++sp) {
+          int4* a = reinterpret_cast<int4*>(g + sp * s.V);
+          const int4* b = reinterpret_cast<const int4*>(cnt + sp * vmax);
+          for (int i = sl; i < V4; i += H) a[i] = b[i];
+        }
+      } else {
+        for (int sp = 0; sp < 3; ++sp)
+          for (int i = sl; i < s.V; i += H) g[sp * s.V + i] = cnt[sp * vmax + i];
+      }
+      const int e_or = static_cast<int>(__reduce_or_sync(segmask, static_cast<unsigned>(err)));
+      if (sl == 0) {
+        sv->ev_last[cell] = e;
+        sv->t_last[cell] = tnow;
+        sv->ev_total[cell] += e;
+        if (e_or) atomicOr(sv->err, e_or);
+      }
+      err = 0;
+      have = false;
+      __syncwarp(segmask);
+    }
+  }
+}
+
+}  // namespace
+
+}  // namespace tsg

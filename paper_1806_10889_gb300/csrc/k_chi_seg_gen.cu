@@ -1,0 +1,21 @@
+// K_chi, persistent segmented form: the instantiations that take tissues of
+// either single-cell model (Notch-Delta or promoter) in one launch.  The
+// kernel template is in chi_seg.cuh.
+#include "chi_seg.cuh"
+
+namespace tsg {
+
+ChiSegKernel chi_seg_kernel_gen(int H, bool pre, bool qb) {
+  if (H == 8) {
+    if (!pre) return k_chi_seg<8, false, false, true>;
+    return qb ? k_chi_seg<8, true, true, true> : k_chi_seg<8, true, false, true>;
+  }
+  if (H == 16) {
+    if (!pre) return k_chi_seg<16, false, false, true>;
+    return qb ? k_chi_seg<16, true, true, true> : k_chi_seg<16, true, false, true>;
+  }
+  if (!pre) return k_chi_seg<32, false, false, true>;
+  return qb ? k_chi_seg<32, true, true, true> : k_chi_seg<32, true, false, true>;
+}
+
+}  // namespace tsg

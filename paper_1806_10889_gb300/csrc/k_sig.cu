@@ -6,7 +6,8 @@
 // A face joins cell c (the owner, the lower id) and its +x (axis 0) or +y
 // (axis 1) neighbour.  Lane p holds voxel pair p -- voxel a_p of c on the
 // face and voxel b_p of the neighbour facing it -- in registers, with the
-// two binding channels D(a)+N(b) -> R(b) and D(b)+N(a) -> R(a).  Within a
+// two binding channels D(a)+N(b) -> R(b) and D(b)+N(a) -> R(a) (promoter
+// model: the conversions Delta(a) -> NICD(b) and Delta(b) -> NICD(a)).  Within a
 // phase no voxel belongs to two faces (the single-face coupling rule,
 // Sec. III-A1), so all faces of the phase run concurrently and
 // deterministically.  The direct-method SSA runs over [0, dt) exactly as in
@@ -43,10 +44,13 @@ __device__ __forceinline__ void sig_face(const TissueView& t, const uint32_t c, 
     Nb = gb[V + vb];
     Rb = gb[2 * V + vb];
   }
+  // Notch-Delta: D(a) + N(b) -> R(b) at k_bind D(a) N(b), and the mirror.
+  // Promoter model: Delta(a) -> NICD(b) at k_N D(a), and the mirror.
+  const bool pm = t.q.kind == kModelPromoter;
   const uint64_t kb = t.q.k_bind;
   bool ovf = false;
-  uint64_t c0 = mul_lim(kb, static_cast<uint64_t>(Da) * Nb, ovf);
-  uint64_t c1 = mul_lim(kb, static_cast<uint64_t>(Db) * Na, ovf);
+  uint64_t c0 = mul_lim(kb, static_cast<uint64_t>(Da) * (pm ? 1u : Nb), ovf);
+  uint64_t c1 = mul_lim(kb, static_cast<uint64_t>(Db) * (pm ? 1u : Na), ovf);
   uint64_t s = c0 + c1;
   uint64_t P = s;
 #pragma unroll
@@ -92,19 +96,19 @@ __device__ __forceinline__ void sig_face(const TissueView& t, const uint32_t c, 
     tnow = tn;
     uint64_t delta = 0;
     if (lane == L) {
-      if (r1 < c0L) {  // D(a) + N(b) -> R(b)
+      if (r1 < c0L) {  // D(a) + N(b) -> R(b), or Delta(a) -> NICD(b)
         Da -= 1;
-        Nb -= 1;
-        Rb += 1;
-        ovf |= Rb > static_cast<uint32_t>(kCountMax);
-      } else {         // D(b) + N(a) -> R(a)
+        Nb = pm ? Nb + 1 : Nb - 1;
+        Rb += pm ? 0 : 1;
+        ovf |= Rb > static_cast<uint32_t>(kCountMax) || Nb > static_cast<uint32_t>(kCountMax);
+      } else {         // D(b) + N(a) -> R(a), or Delta(b) -> NICD(a)
         Db -= 1;
-        Na -= 1;
-        Ra += 1;
-        ovf |= Ra > static_cast<uint32_t>(kCountMax);
+        Na = pm ? Na + 1 : Na - 1;
+        Ra += pm ? 0 : 1;
+        ovf |= Ra > static_cast<uint32_t>(kCountMax) || Na > static_cast<uint32_t>(kCountMax);
       }
-      c0 = mul_lim(kb, static_cast<uint64_t>(Da) * Nb, ovf);
-      c1 = mul_lim(kb, static_cast<uint64_t>(Db) * Na, ovf);
+      c0 = mul_lim(kb, static_cast<uint64_t>(Da) * (pm ? 1u : Nb), ovf);
+      c1 = mul_lim(kb, static_cast<uint64_t>(Db) * (pm ? 1u : Na), ovf);
       const uint64_t s2 = c0 + c1;
       delta = s2 - s;
       s = s2;

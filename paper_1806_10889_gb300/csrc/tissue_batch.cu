@@ -29,6 +29,7 @@ struct ClassPlan {
   uint32_t lanes, warps_per_block, layout;
   size_t items_off;  // offset (in uint2) into the item buffer
   uint32_t n_items;
+  bool gen;          // some member of the class runs the promoter model
 };
 
 }  // namespace
@@ -58,7 +59,7 @@ int chi_all(tissue_batch* b, double dt) {
       return TISSUE_E_CUDA;
     if (launch_chi_seg(b->d_views, b->d_items + p.items_off, p.n_items, b->d_counters + c, p.V,
                        static_cast<int>(p.lanes), static_cast<int>(p.warps_per_block), 0, 0u, dt,
-                       p.layout == TISSUE_LAYOUT_PREFIX, b->stream) != cudaSuccess)
+                       p.layout == TISSUE_LAYOUT_PREFIX, p.gen, b->stream) != cudaSuccess)
       return TISSUE_E_CUDA;
   }
   return TISSUE_OK;
@@ -117,11 +118,13 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
 
   // chi items by class, largest cells first; faces of both phases
   std::map<uint32_t, std::vector<uint2>, std::greater<uint32_t>> by_v;
+  std::map<uint32_t, bool> gen_v;
   std::vector<uint2> xf, yf;
   for (uint32_t i = 0; i < count; ++i) {
     const tissue_desc& d = info[i].desc;
     const uint32_t V = d.n * d.n, cells = d.width * d.height;
     std::vector<uint2>& list = by_v[V];
+    gen_v[V] = gen_v[V] || info[i].view.q.kind != kModelND;
     for (uint32_t c = 0; c < cells; ++c) list.push_back(make_uint2(i, c));
     for (uint32_t c = 0; c < cells; ++c) {
       const uint32_t cx = c % d.width, cy = c / d.width;
@@ -139,6 +142,7 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
     p.layout = dl.smem_layout;
     p.items_off = items.size();
     p.n_items = static_cast<uint32_t>(kv.second.size());
+    p.gen = gen_v[kv.first];
     items.insert(items.end(), kv.second.begin(), kv.second.end());
     b->classes.push_back(p);
   }

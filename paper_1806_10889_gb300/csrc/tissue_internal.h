@@ -15,10 +15,16 @@ constexpr uint32_t kHillTab = 4096;  // tabulated Hill production for R < kHillT
 constexpr int kErrOverflow = 1;
 constexpr int kErrEventIndex = 2;
 constexpr int kErrInternal = 4;  // a selection invariant failed (never expected)
+constexpr int kErrState = 8;     // promoter model: more bound sites than sites in a voxel
+constexpr uint32_t kModelND = 0u;        // Hill-repressed Notch-Delta lattice model
+constexpr uint32_t kModelPromoter = 1u;  // the paper's promoter model (Sec. III-A1)
 constexpr int kCountMax = (1 << 30) - 1;      // largest count a voxel may hold
 constexpr uint64_t kPropLimit = 1ull << 52;  // a voxel or face channel must stay below
 
 // Quantised model: every rate as an integer in units of 2^-32 per unit time.
+// The promoter model maps onto the same fields: gD = gN = d, hopD = hopN =
+// hop, k_in = k_a (slot 17, X = N F), k_bind = k_N (face conversion), and
+// gR = hopR = k_off = kN = 0; tD and kd are its own.
 struct QRates {
   uint64_t kN, gD, gN, gR, hopD, hopN, hopR, k_in, k_off, k_bind;
   uint64_t cD[5], cN[5], cR[5];  // g + nn * hop for nn existing neighbours
@@ -26,6 +32,8 @@ struct QRates {
   double kD, K;
   const uint64_t* hill;  // device table, kHillTab entries
   uint32_t small;        // counts all below this keep every voxel total below 2^52
+  uint32_t kind;         // kModelND or kModelPromoter
+  uint64_t tD, kd;       // promoter: transcription by a free site, unbinding of a bound one
 };
 
 // One tissue as the kernels see it.
@@ -55,10 +63,16 @@ cudaError_t launch_chi(const TissueView& t, uint32_t step_off, double dt, int wa
 // picks a grid that fills every SM.
 // pre: keep the per-voxel prefix array (layout 0) or recompute the selected
 // block (layout 1, at most 4 warps per block).
+// gen: the launch may hold promoter-model tissues (instantiations that test
+// each tissue's model); false runs the Notch-Delta-only code.
 cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
                            uint32_t* d_counter, uint32_t vmax_cells, int H, int warps_per_block,
-                           int blocks, uint32_t step_off, double dt, bool pre,
+                           int blocks, uint32_t step_off, double dt, bool pre, bool gen,
                            cudaStream_t stream);
+using ChiSegKernel = void (*)(const TissueView*, const uint2*, uint32_t, uint32_t*, uint32_t,
+                              uint32_t, double);
+ChiSegKernel chi_seg_kernel_nd(int H, bool pre, bool qb);   // k_chi_seg.cu
+ChiSegKernel chi_seg_kernel_gen(int H, bool pre, bool qb);  // k_chi_seg_gen.cu
 uint32_t seg_bytes_for(uint32_t V, int H, bool pre);
 cudaError_t launch_sig_list(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
                             int axis, uint32_t tag, double dt, cudaStream_t stream);
@@ -88,6 +102,9 @@ cudaError_t launch_selftest_time(uint64_t n, uint64_t seed, unsigned long long* 
 // hopR, k_in, k_off, k_bind) into q; q->hill is set to `hill`.  false when a
 // rate is out of range.
 bool make_qrates(const double rates[12], const uint64_t* hill, QRates* q);
+// The promoter model (tD, ka, kd, kN, d, hop) into q; false when a rate is out
+// of range.
+bool make_qrates_promoter(const double rates[6], const uint64_t* hill, QRates* q);
 
 // Largest power of two T <= 2^30 such that counts below T keep a voxel's total
 // propensity below 2^52 (so the fast path needs no overflow checks).

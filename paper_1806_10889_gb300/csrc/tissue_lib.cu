@@ -119,7 +119,8 @@ cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt
     return launch_chi_seg(t->d_view, nullptr, t->d.width * t->d.height, t->d_work, v.V,
                           static_cast<int>(c.lanes_per_cell), static_cast<int>(c.warps_per_block),
                           static_cast<int>(c.blocks), i, dt,
-                          c.smem_layout == TISSUE_LAYOUT_PREFIX, t->stream);
+                          c.smem_layout == TISSUE_LAYOUT_PREFIX, t->q.kind != kModelND,
+                          t->stream);
   }
   return launch_chi(v, i, dt, static_cast<int>(c.warps_per_block), t->stream);
 }
@@ -154,7 +155,13 @@ int device_error(tissue* t) {
     return TISSUE_E_CUDA;
   if (cudaStreamSynchronize(t->stream) != cudaSuccess) return TISSUE_E_CUDA;
   if (h & kErrInternal) return TISSUE_E_CUDA;
+  if (h & kErrState) return TISSUE_E_STATE;
   return h ? TISSUE_E_OVERFLOW : TISSUE_OK;
+}
+
+// The one-warp-per-cell kernel computes the Notch-Delta model only.
+bool launch_fits_model(const tissue* t) {
+  return t->q.kind == kModelND || t->cfg.kernel == TISSUE_KERNEL_PERSISTENT;
 }
 
 bool rate_ok(double x) { return std::isfinite(x) && x >= 0.0 && x < 1048576.0; }
@@ -190,6 +197,28 @@ bool tsg::make_qrates(const double r[12], const uint64_t* hill, QRates* q) {
   q->hill = hill;
   // the Hill term is largest at R = 0, where it is quantise(kD) (kD / 1)
   q->small = small_count_bound(*q, quantise(r[0]));
+  return true;
+}
+
+bool tsg::make_qrates_promoter(const double r[6], const uint64_t* hill, QRates* q) {
+  for (int i = 0; i < 6; ++i)
+    if (!rate_ok(r[i])) return false;
+  *q = QRates{};
+  q->kind = kModelPromoter;
+  q->tD = quantise(r[0]);
+  q->k_in = quantise(r[1]);    // k_a: slot 17, N + F -> R
+  q->kd = quantise(r[2]);
+  q->k_bind = quantise(r[3]);  // k_N: Delta -> NICD across a face
+  q->gD = q->gN = quantise(r[4]);
+  q->hopD = q->hopN = quantise(r[5]);
+  q->K = 1.0;
+  for (int nn = 0; nn <= 4; ++nn) {
+    q->cD[nn] = q->gD + static_cast<uint64_t>(nn) * q->hopD;
+    q->cN[nn] = q->gN + static_cast<uint64_t>(nn) * q->hopN;
+  }
+  q->hill = hill;
+  // c0 + c1 = tD F + kd R <= max(tD, kd) since F + R <= 1
+  q->small = small_count_bound(*q, q->tD > q->kd ? q->tD : q->kd);
   return true;
 }
 
@@ -281,6 +310,19 @@ int tissue_set_model(tissue* t, const tissue_model* m) {
   return TISSUE_OK;
 }
 
+int tissue_set_promoter_model(tissue* t, const tissue_promoter_model* m) {
+  if (!t || !m) return TISSUE_E_ARG;
+  const double r[6] = {m->tD, m->ka, m->kd, m->kN, m->d, m->hop};
+  QRates q{};
+  if (!make_qrates_promoter(r, t->hill, &q)) return TISSUE_E_ARG;
+  t->q = q;
+  const TissueView v = view_of(t);
+  if (cudaMemcpyAsync(t->d_view, &v, sizeof(v), cudaMemcpyHostToDevice, t->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  t->has_model = true;
+  return TISSUE_OK;
+}
+
 int tissue_write_counts(tissue* t, const int32_t* host, size_t n, uint32_t step_index) {
   if (!t || !host) return TISSUE_E_ARG;
   const size_t want = tissue_state_bytes(&t->d) / sizeof(int32_t);
@@ -302,7 +344,7 @@ int tissue_write_counts(tissue* t, const int32_t* host, size_t n, uint32_t step_
 int tissue_step(tissue* t, double dt, uint32_t n_steps) {
   if (!t) return TISSUE_E_ARG;
   if (!t->has_model) return TISSUE_E_NOMODEL;
-  if (!(dt > 0.0) || !std::isfinite(dt)) return TISSUE_E_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt) || !launch_fits_model(t)) return TISSUE_E_ARG;
   if (n_steps == 0) return TISSUE_OK;
   const TissueView v = view_of(t);
   for (uint32_t i = 0; i < n_steps; ++i) {
@@ -317,7 +359,7 @@ int tissue_step(tissue* t, double dt, uint32_t n_steps) {
 int tissue_step_timed(tissue* t, double dt, uint32_t n_steps, double* ms_chi, double* ms_sig) {
   if (!t) return TISSUE_E_ARG;
   if (!t->has_model) return TISSUE_E_NOMODEL;
-  if (!(dt > 0.0) || !std::isfinite(dt)) return TISSUE_E_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt) || !launch_fits_model(t)) return TISSUE_E_ARG;
   // per step: start, chi start, chi end, end
   std::vector<cudaEvent_t> ev(4 * static_cast<size_t>(n_steps), nullptr);
   int rc = TISSUE_OK;
@@ -478,6 +520,7 @@ const char* tissue_strerror(int code) {
     case TISSUE_E_CUDA: return "CUDA runtime error";
     case TISSUE_E_TIMEOUT: return "device wait timed out";
     case TISSUE_E_BUDGET: return "memory budget exceeded";
+    case TISSUE_E_STATE: return "more bound promoter sites than sites";
     default: return "unknown error";
   }
 }

@@ -23,6 +23,7 @@ _lib = None
 DEFAULT_CHI_WPB = 4
 
 OK, E_ARG, E_NOMEM, E_NOMODEL, E_OVERFLOW, E_CUDA, E_TIMEOUT, E_BUDGET = 0, -1, -2, -3, -4, -5, -6, -7
+E_STATE = -9
 
 
 class TissueError(RuntimeError):
@@ -46,6 +47,13 @@ class Model(C.Structure):
     _fields_ = [(f, C.c_double) for f in MODEL_FIELDS]
 
 
+PROMOTER_FIELDS = ["tD", "ka", "kd", "kN", "d", "hop"]
+
+
+class PromoterModel(C.Structure):
+    _fields_ = [(f, C.c_double) for f in PROMOTER_FIELDS]
+
+
 KERNEL_WARP, KERNEL_PERSISTENT = 0, 1
 LAYOUT_PREFIX, LAYOUT_RECOMPUTE = 0, 1
 SPLIT_LIE, SPLIT_STRANG = 0, 1
@@ -64,6 +72,7 @@ SIGNATURES = {
     "tissue_scratch_bytes": (C.c_size_t, [_P(Desc)]),
     "tissue_create": (C.c_int, [_P(Desc), C.c_void_p, C.c_size_t, C.c_void_p, _P(C.c_void_p)]),
     "tissue_set_model": (C.c_int, [C.c_void_p, _P(Model)]),
+    "tissue_set_promoter_model": (C.c_int, [C.c_void_p, _P(PromoterModel)]),
     "tissue_write_counts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint32]),
     "tissue_step": (C.c_int, [C.c_void_p, C.c_double, C.c_uint32]),
     "tissue_step_timed": (C.c_int, [C.c_void_p, C.c_double, C.c_uint32, _P(C.c_double),
@@ -127,7 +136,14 @@ def desc_of(spec: TissueSpec) -> Desc:
     return d
 
 
-def model_of(model: dict) -> Model:
+def model_of(model: dict):
+    """The C struct of a model dict: PromoterModel if model["kind"] is
+    "promoter", else the Notch-Delta Model."""
+    if model.get("kind") == "promoter":
+        p = PromoterModel()
+        for f in PROMOTER_FIELDS:
+            setattr(p, f, float(model[f]))
+        return p
     m = Model()
     for f in MODEL_FIELDS:
         setattr(m, f, float(model[f]))
@@ -195,7 +211,11 @@ class Tissue:
 
     def set_model(self, model: dict):
         self._model = model_of(model)
-        _check(lib().tissue_set_model(self._h, C.byref(self._model)), "tissue_set_model")
+        if isinstance(self._model, PromoterModel):
+            _check(lib().tissue_set_promoter_model(self._h, C.byref(self._model)),
+                   "tissue_set_promoter_model")
+        else:
+            _check(lib().tissue_set_model(self._h, C.byref(self._model)), "tissue_set_model")
 
     def set_launch(self, chi_warps_per_block: int):
         _check(lib().tissue_set_launch(self._h, int(chi_warps_per_block)), "tissue_set_launch")

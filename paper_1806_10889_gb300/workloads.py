@@ -26,6 +26,31 @@ ND_MODEL = dict(kD=10.0, K=20.0, kN=5.0, gD=0.1, gN=0.1, gR=0.2,
                 hopD=1.0, hopN=1.0, hopR=1.0, k_in=0.0, k_off=0.0, k_bind=0.01)
 
 
+# The paper's Notch model (Sec. III-A1, Table I): diffusion constant 1e-12 m^2/s,
+# transcription t_D = 100/s, DNA binding k_a = 1e-18 m^3/s, unbinding
+# k_d = 25/s, Delta -> NICD k_N = 1/s; every species but DNA decays at a rate d
+# the paper does not give (1/s here).  Cells are cubes of side 1 um (the
+# network file's "wsize", Fig. 2).  On an n x n lattice each voxel is a column
+# of h x h x L (h = L/n), so the hop rate per direction is D/h^2 = n^2 per s
+# and the binding rate per NICD molecule in the promoter's voxel is
+# k_a / (h^2 L) = n^2 per s.  Time unit: seconds, dt = 0.1 s (the network
+# file's end_time).
+CELL_SIDE_M = 1e-6
+TABLE1 = dict(D=1e-12, tD=100.0, ka=1e-18, kd=25.0, kN=1.0)
+PROMOTER_DECAY = 1.0
+
+
+def promoter_model(n: int, d: float = PROMOTER_DECAY) -> dict:
+    """Table I in lattice units for cells of n x n voxels (see above)."""
+    h = CELL_SIDE_M / n
+    return dict(kind="promoter", tD=TABLE1["tD"], ka=TABLE1["ka"] / (h * h * CELL_SIDE_M),
+                kd=TABLE1["kd"], kN=TABLE1["kN"], d=d, hop=TABLE1["D"] / (h * h))
+
+
+def is_promoter(model: dict) -> bool:
+    return model.get("kind") == "promoter"
+
+
 @dataclass(frozen=True)
 class TissueSpec:
     """One tissue: geometry, random key and model (plain numbers only)."""
@@ -73,6 +98,16 @@ def medium(dt: float = 0.1) -> Run:
         raise ValueError("medium tissue is defined for dt in {0.01, 0.1, 1.0}")
     return Run(TissueSpec(64, 64, 16, seed=2, tissue_id=0), dt=dt,
                n_steps=int(round(50.0 / dt)))
+
+
+def promoter(side: int = 64, n: int = 16, dt: float = 0.1, n_steps: int = 500) -> Run:
+    """The promoter model on a side x side tissue of n x n-voxel cells, seed 6.
+    Initial Delta and NICD Poisson(0.2) and Poisson(0.05) per voxel (about
+    the steady state of 16x16 cells: ~50 Delta and ~12 NICD per cell), every
+    promoter free."""
+    spec = TissueSpec(side, side, n, seed=6, tissue_id=0, init_lambda=(0.2, 0.05, 0.0),
+                      model=promoter_model(n))
+    return Run(spec, dt=dt, n_steps=n_steps)
 
 
 def large() -> Run:

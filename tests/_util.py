@@ -17,7 +17,9 @@ def orc_desc(spec: TissueSpec) -> O.Desc:
                   init_lambda=tuple(spec.init_lambda))
 
 
-def orc_model(spec: TissueSpec) -> O.Model:
+def orc_model(spec: TissueSpec):
+    if spec.model.get("kind") == "promoter":
+        return O.Promoter(**{k: v for k, v in spec.model.items() if k != "kind"})
     return O.Model(**spec.model)
 
 

@@ -54,7 +54,7 @@ def build(force: bool = False) -> str:
 class _Desc(C.Structure):
     _fields_ = [("width", C.c_uint32), ("height", C.c_uint32), ("n", C.c_uint32),
                 ("tissue_id", C.c_uint32), ("seed", C.c_uint64),
-                ("init_lambda", C.c_double * 3)]
+                ("init_lambda", C.c_double * 3), ("wm", C.c_void_p)]
 
 
 _MODEL_FIELDS = ["kD", "K", "kN", "gD", "gN", "gR", "hopD", "hopN", "hopR",
@@ -94,6 +94,13 @@ class Desc:
     seed: int
     tissue_id: int = 0
     init_lambda: tuple = (5.0, 5.0, 5.0)
+    wm: np.ndarray | None = None  # per cell: 1 = well-mixed chi, 0 = lattice RDME
+
+    def __post_init__(self):
+        if self.wm is not None:
+            self.wm = np.ascontiguousarray(self.wm, dtype=np.uint8)
+            if self.wm.size != self.width * self.height:
+                raise ValueError("wm needs one entry per cell")
 
     @property
     def cells(self) -> int:
@@ -108,6 +115,7 @@ class Desc:
         d.width, d.height, d.n = self.width, self.height, self.n
         d.tissue_id, d.seed = self.tissue_id, self.seed
         d.init_lambda = (C.c_double * 3)(*self.init_lambda)
+        d.wm = self.wm.ctypes.data if self.wm is not None else None
         return d
 
 

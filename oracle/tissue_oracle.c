@@ -154,6 +154,7 @@ typedef struct {
   uint64_t kN, gD, gN, gR, hopD, hopN, hopR, k_in, k_off, k_bind;
   double kD, K;
   uint64_t tD, ka, kd, kNc, d, hop;  /* promoter model (kNc: the face's k_N) */
+  double k_in_raw, ka_raw;           /* for the well-mixed compartment rates */
 } qmodel;
 
 int orc_validate(const orc_desc* d, const orc_model* m) {
@@ -194,6 +195,7 @@ static int make_qmodel(const orc_model* m, qmodel* q) {
     orc_quantize(m->pm.kN, &q->kNc);
     orc_quantize(m->pm.d, &q->d);
     orc_quantize(m->pm.hop, &q->hop);
+    q->ka_raw = m->pm.ka;
     return ORC_OK;
   }
   orc_quantize(m->kN, &q->kN);
@@ -209,6 +211,7 @@ static int make_qmodel(const orc_model* m, qmodel* q) {
   if (g_mutation == 3) q->gR = q->gD;
   q->kD = m->kD;
   q->K = m->K;
+  q->k_in_raw = m->k_in;
   return ORC_OK;
 }
 
@@ -450,6 +453,118 @@ static int chi_cell_q(const orc_desc* d, const qmodel* q, int32_t* counts, uint3
   return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* chi of a well-mixed cell (see the header): totals, direct-method SSA on    */
+/* the totals, uniform placement.                                             */
+/* ------------------------------------------------------------------------ */
+#define WM_NCH 7
+
+static int wm_channels(const qmodel* q, int V, const int64_t T[3], u128 a[WM_NCH]) {
+  for (int j = 0; j < WM_NCH; ++j) a[j] = 0;
+  const uint64_t D = (uint64_t)T[0], N = (uint64_t)T[1], R = (uint64_t)T[2];
+  uint64_t k17;
+  if (q->kind == ORC_MODEL_PROMOTER) {
+    const uint64_t F = 1 - R;
+    if (orc_quantize(q->ka_raw / (double)V, &k17)) return ORC_E_ARG;
+    a[0] = (u128)q->tD * F;
+    a[1] = (u128)q->kd * R;
+    a[2] = (u128)q->d * D;
+    a[3] = (u128)q->d * N;
+    a[4] = (u128)k17 * (N * F);
+    return ORC_OK;
+  }
+  const double Kc = (g_mutation == 12) ? q->K : (double)V * q->K;
+  const double x = (double)R / Kc;
+  const double val = ((double)V * q->kD) / (1.0 + x * x);
+  if (orc_quantize(q->k_in_raw / (double)V, &k17)) return ORC_E_ARG;
+  a[0] = (uint64_t)nearbyint(val * 4294967296.0);
+  a[1] = (u128)q->kN * (uint64_t)V;
+  a[2] = (u128)q->gD * D;
+  a[3] = (u128)q->gN * N;
+  a[4] = (u128)q->gR * R;
+  a[5] = (u128)k17 * ((u128)D * N);
+  a[6] = (u128)q->k_off * R;
+  return ORC_OK;
+}
+
+/* The voxel of the i-th placed molecule of species s. */
+static int wm_voxel(const orc_desc* d, uint32_t c, uint32_t step, int s, uint64_t i, int V) {
+  uint32_t w[4];
+  draw(d, (uint32_t)(i >> 2), step, c, d->tissue_id | ((ORC_TAG_PLACE + (uint32_t)s) << 24), w);
+  const uint64_t v = ((uint64_t)w[i & 3] * (uint64_t)V) >> 32;
+  if (g_mutation == 11 && v == (uint64_t)(V - 1)) return 0;
+  return (int)v;
+}
+
+static int wm_cell_q(const orc_desc* d, const qmodel* q, int32_t* counts, uint32_t c,
+                     uint32_t step, double dt, uint64_t* n_events, double* t_last,
+                     orc_event* trace, size_t cap, size_t* len) {
+  const int n = (int)d->n, V = n * n;
+  int32_t* cell = counts + (size_t)c * 3 * V;
+  const int pm = q->kind == ORC_MODEL_PROMOTER;
+  int64_t T[3] = {0, 0, 0};
+  int rc = ORC_OK;
+  for (int sp = 0; sp < 3; ++sp)
+    for (int v = 0; v < V; ++v) T[sp] += cell[sp * V + v];
+  if (pm)
+    for (int v = 0; v < V; ++v)
+      if (cell[ORC_R * V + v] > (v == centre_voxel(n))) rc = ORC_E_STATE;
+  for (int sp = 0; sp < 3; ++sp)
+    if (T[sp] > ORC_COUNT_MAX) rc = rc ? rc : ORC_E_OVERFLOW;
+  double t = 0.0;
+  uint32_t e = 0;
+  while (rc == ORC_OK) {
+    u128 a[WM_NCH], A128 = 0;
+    if ((rc = wm_channels(q, V, T, a))) break;
+    for (int j = 0; j < WM_NCH; ++j) A128 += a[j];
+    if (A128 >= (u128)ORC_PROP_LIMIT) { rc = ORC_E_OVERFLOW; break; }
+    const uint64_t A = (uint64_t)A128;
+    if (A == 0) break;
+    uint32_t w[4];
+    draw(d, e, step, c, d->tissue_id | (ORC_TAG_CHI << 24), w);
+    const double E = orc_exp_variate(w[0], w[1]);
+    const double tn = t + E / ((double)A * 0x1p-32);
+    if (!(tn < dt)) break;
+    t = tn;
+    const uint64_t R64 = ((uint64_t)w[3] << 32) | w[2];
+    uint64_t r = (uint64_t)(((u128)R64 * A) >> 64);
+    int j = 0;
+    while ((u128)r >= a[j]) { r -= (uint64_t)a[j]; ++j; }
+    record(trace, cap, len, step, ORC_TAG_CHI, c, e, t, 0u, (uint32_t)j);
+    static const int dnd[WM_NCH][3] = {{1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
+                                       {0, 0, -1}, {-1, -1, 1}, {1, 1, -1}};
+    static const int dpm[WM_NCH][3] = {{1, 0, 0}, {0, 1, -1}, {-1, 0, 0}, {0, -1, 0},
+                                       {0, -1, 1}, {0, 0, 0}, {0, 0, 0}};
+    for (int sp = 0; sp < 3; ++sp) {
+      T[sp] += pm ? dpm[j][sp] : dnd[j][sp];
+      if (T[sp] < 0 || T[sp] > ORC_COUNT_MAX) rc = ORC_E_OVERFLOW;
+    }
+    e += 1;
+    if (e == 0xFFFFFFFFu) rc = ORC_E_OVERFLOW;
+  }
+  if (rc == ORC_OK) { /* placement */
+    memset(cell, 0, sizeof(int32_t) * 3 * V);
+    for (int sp = 0; sp < 3; ++sp) {
+      if (pm && sp == ORC_R) {
+        cell[ORC_R * V + centre_voxel(n)] = (int32_t)T[ORC_R];
+        continue;
+      }
+      for (int64_t i = 0; i < T[sp]; ++i) cell[sp * V + wm_voxel(d, c, step, sp, (uint64_t)i, V)] += 1;
+    }
+  }
+  if (n_events) *n_events = e;
+  if (t_last) *t_last = t;
+  return rc;
+}
+
+static int chi_any_q(const orc_desc* d, const qmodel* q, int32_t* counts, uint32_t c,
+                     uint32_t step, double dt, uint64_t* n_events, double* t_last,
+                     orc_event* trace, size_t cap, size_t* len) {
+  if (d->wm && d->wm[c])
+    return wm_cell_q(d, q, counts, c, step, dt, n_events, t_last, trace, cap, len);
+  return chi_cell_q(d, q, counts, c, step, dt, n_events, t_last, trace, cap, len);
+}
+
 int orc_chi_cell(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_t c,
                  uint32_t step, double dt, uint64_t* n_events, double* t_last,
                  orc_event* trace, size_t trace_cap, size_t* trace_len) {
@@ -459,7 +574,7 @@ int orc_chi_cell(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_
   if (!(dt > 0.0) || !isfinite(dt)) return ORC_E_ARG;
   make_qmodel(m, &q);
   if (c >= d->width * d->height) return ORC_E_ARG;
-  return chi_cell_q(d, &q, counts, c, step, dt, n_events, t_last, trace, trace_cap, trace_len);
+  return chi_any_q(d, &q, counts, c, step, dt, n_events, t_last, trace, trace_cap, trace_len);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -605,7 +720,7 @@ static int chi_phase(const orc_desc* d, const qmodel* q, int32_t* counts, uint32
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads) reduction(| : err)
   for (int64_t c = 0; c < cells; ++c) {
     uint64_t ne; double tl;
-    err |= -chi_cell_q(d, q, counts, (uint32_t)c, k, dt, &ne, &tl, trace, cap, len);
+    err |= -chi_any_q(d, q, counts, (uint32_t)c, k, dt, &ne, &tl, trace, cap, len);
     if (last && n_events) n_events[c] = ne;
     if (last && t_last) t_last[c] = tl;
   }

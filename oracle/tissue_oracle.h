@@ -47,6 +47,7 @@ extern "C" {
 #define ORC_TAG_INIT 4u
 #define ORC_TAG_SX2 5u   /* second half-step of x-faces (Strang splitting) */
 #define ORC_TAG_SY2 6u   /* second half-step of y-faces (Strang splitting) */
+#define ORC_TAG_PLACE 7u /* placement of a well-mixed cell's D (7), N (8), R (9) */
 
 /* Species index in the state layout counts[cell][species][voxel]. */
 #define ORC_D 0
@@ -63,6 +64,7 @@ typedef struct {
   uint32_t tissue_id;       /* < 2^24 */
   uint64_t seed;            /* Philox key */
   double init_lambda[3];    /* Poisson mean of the initial count of D, N, R per voxel */
+  const uint8_t* wm;        /* per cell: 0 lattice RDME, 1 well-mixed; NULL = all lattice */
 } orc_desc;
 
 /* The paper's own Notch model (Sec. III-A1, Table I) on the voxel lattice.
@@ -92,6 +94,31 @@ typedef struct {
   int32_t reserved;
   orc_promoter pm;          /* used when kind == ORC_MODEL_PROMOTER */
 } orc_model;
+
+/* Well-mixed cells (the coarse single-cell module of the paper's mixed-
+ * fidelity tissues, Sec. IV).  A well-mixed cell keeps its molecules in the
+ * same voxel layout between module calls, but its chi ignores position:
+ *   1. T_{S->chi}: the totals of D, N, R over the cell's voxels;
+ *   2. the direct-method SSA on the totals over [0, dt), with the cell as one
+ *      compartment of V voxel volumes:
+ *        Notch-Delta   0 D production V kD / (1 + (R / (V K))^2)
+ *                      1 N production V kN
+ *                      2..4 decay gD D, gN N, gR R
+ *                      5 D + N -> R at (k_in / V) D N
+ *                      6 R -> D + N at k_off R
+ *        promoter      0 transcription t_D F (F = 1 - R, one site per cell)
+ *                      1 unbinding k_d R
+ *                      2, 3 decay d D, d N
+ *                      4 binding (k_a / V) N F
+ *   3. T_{chi->S}: every molecule is placed in a voxel drawn uniformly at
+ *      random (the well-mixed assumption), v = floor(w V / 2^32) with w the
+ *      (i mod 4)-th word of Philox block (i / 4, step, cell, tissue_id |
+ *      (7 + species) << 24) for the i-th molecule of the species; the
+ *      promoter model's bound site stays on the promoter voxel.
+ * The Hill term is evaluated in binary64 as written, left to right, each
+ * operation rounded to nearest, then quantised; k_in / V and k_a / V are one
+ * binary64 division each, then quantised.  On an error the cell's counts are
+ * left unchanged. */
 
 /* One fired event, for full-trace comparisons on small cases. */
 typedef struct {

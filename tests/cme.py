@@ -206,3 +206,190 @@ def split_law(W, H, n, rates, x0, dt, k_steps, scheme="lie", model="nd", max_del
         for _ in range(k_steps):
             p = hx @ (hy @ (chi @ (hy @ (hx @ p))))
     return states, idx, p, Q
+
+
+# ---- tissues with well-mixed cells (promoter model) -----------------------
+#
+# A well-mixed cell's chi ignores position: it runs the SSA on the cell's
+# totals, then places every molecule in a uniformly random voxel (the bound
+# promoter site stays on the promoter voxel).  As a Markov kernel on full
+# voxel states that is  K_chi = Place . exp(Q_hyb dt) . Aggregate,  where the
+# hybrid state keeps the lattice cells' voxels and the well-mixed cells'
+# totals, and Q_hyb is the sum of the lattice RDME generator and the
+# well-mixed generators (cells are independent within chi).
+
+def _wm_total_moves(r, V, T):
+    """(rate, new totals) of a well-mixed promoter cell with totals T = (D, N, R)."""
+    D, N, R = T
+    F = 1 - R
+    out = []
+    ka_c = r["ka_cell"]
+    if F and r["tD"]:
+        out.append((r["tD"] * F, (D + 1, N, R)))
+    if R and r["kd"]:
+        out.append((r["kd"] * R, (D, N + 1, R - 1)))
+    if D and r["d"]:
+        out.append((r["d"] * D, (D - 1, N, R)))
+    if N and r["d"]:
+        out.append((r["d"] * N, (D, N - 1, R)))
+    if N and F and ka_c:
+        out.append((ka_c * N * F, (D, N - 1, R + 1)))
+    return out
+
+
+def _placements(n, total, centre=None):
+    """Every voxel vector of `total` molecules over n*n voxels with its
+    multinomial probability (all at `centre` if given)."""
+    V = n * n
+    if centre is not None:
+        vec = [0] * V
+        vec[centre] = total
+        return [(tuple(vec), 1.0)]
+    out = []
+
+    def rec(i, left, vec):
+        if i == V - 1:
+            vec = vec + [left]
+            # multinomial: total! / prod(k!) * V^-total
+            from math import factorial
+            p = factorial(total)
+            for k in vec:
+                p //= factorial(k)
+            out.append((tuple(vec), p / V ** total))
+            return
+        for k in range(left + 1):
+            rec(i + 1, left - k, vec + [k])
+
+    rec(0, total, [])
+    return out
+
+
+def wm_split_law(W, H, n, rates, x0, dt, k_steps, wm):
+    """Exact law of the Lie-split promoter model on a tissue whose cells with
+    wm[c] = 1 are well-mixed.  rates: the quantised lattice rates plus
+    "ka_cell", the quantised compartment binding rate k_a / V."""
+    V = n * n
+    C = W * H
+    centre = (n // 2) * n + n // 2
+    lattice = [c for c in range(C) if not wm[c]]
+    mixed = [c for c in range(C) if wm[c]]
+
+    def hyb(x):
+        part = tuple(x[_idx(n, c, s, v)] for c in lattice for s in range(3) for v in range(V))
+        tot = tuple(sum(x[_idx(n, c, s, v)] for v in range(V)) for c in mixed for s in range(3))
+        return part + tot
+
+    def full_from(h, placements_of):
+        """All full states (with probabilities) of hybrid state h."""
+        base = [0] * (C * 3 * V)
+        k = 0
+        for c in lattice:
+            for s in range(3):
+                for v in range(V):
+                    base[_idx(n, c, s, v)] = h[k]
+                    k += 1
+        outs = [(base, 1.0)]
+        for j, c in enumerate(mixed):
+            T = h[k + 3 * j:k + 3 * j + 3]
+            new = []
+            for vec, p in outs:
+                for pd, qd in placements_of(T[0], None):
+                    for pn, qn in placements_of(T[1], None):
+                        for pr, qr in placements_of(T[2], centre):
+                            y = list(vec)
+                            for v in range(V):
+                                y[_idx(n, c, 0, v)] = pd[v]
+                                y[_idx(n, c, 1, v)] = pn[v]
+                                y[_idx(n, c, 2, v)] = pr[v]
+                            new.append((y, p * qd * qn * qr))
+            outs = new
+        return [(tuple(y), p) for y, p in outs]
+
+    cache = {}
+
+    def placements_of(total, ctr):
+        key = (total, ctr)
+        if key not in cache:
+            cache[key] = _placements(n, total, ctr)
+        return cache[key]
+
+    def hyb_moves(h):
+        x = full_from(h, lambda t, ctr: [(tuple([t] + [0] * (V - 1)), 1.0)] if ctr is None
+                      else [(tuple(t if v == ctr else 0 for v in range(V)), 1.0)])[0][0]
+        out = []
+        # lattice cells: RDME moves on their voxels
+        for rate, y in promoter_chi_moves(W, H, n, rates, x):
+            changed = {i // (3 * V) for i in range(len(x)) if x[i] != y[i]}
+            if changed <= set(lattice):
+                out.append((rate, hyb(y)[:len(h) - 3 * len(mixed)] + h[len(h) - 3 * len(mixed):]))
+        k0 = len(h) - 3 * len(mixed)
+        for j in range(len(mixed)):
+            T = h[k0 + 3 * j:k0 + 3 * j + 3]
+            for rate, T2 in _wm_total_moves(rates, V, T):
+                out.append((rate, h[:k0 + 3 * j] + tuple(T2) + h[k0 + 3 * j + 3:]))
+        return out
+
+    # closure of full states and hybrid states
+    x0 = tuple(int(v) for v in x0)
+    full_idx, fulls = {x0: 0}, [x0]
+    hyb_idx, hybs = {}, []
+    qf = deque([x0])
+
+    def add_full(y):
+        if y not in full_idx:
+            full_idx[y] = len(fulls)
+            fulls.append(y)
+            qf.append(y)
+
+    def add_hyb(h):
+        if h in hyb_idx:
+            return False
+        hyb_idx[h] = len(hybs)
+        hybs.append(h)
+        return True
+
+    while qf:
+        x = qf.popleft()
+        for axis in (0, 1):
+            for _, y in promoter_sig_moves(W, H, n, rates, x, axis):
+                add_full(y)
+        h0 = hyb(x)
+        if add_hyb(h0):
+            qh = deque([h0])
+            while qh:
+                h = qh.popleft()
+                for y, _ in full_from(h, placements_of):
+                    add_full(y)
+                for _, h2 in hyb_moves(h):
+                    if add_hyb(h2):
+                        qh.append(h2)
+    S, Hn = len(fulls), len(hybs)
+    A = np.zeros((Hn, S))
+    for i, x in enumerate(fulls):
+        A[hyb_idx[hyb(x)], i] = 1.0
+    Qh = np.zeros((Hn, Hn))
+    for i, h in enumerate(hybs):
+        for rate, h2 in hyb_moves(h):
+            j = hyb_idx[h2]
+            Qh[j, i] += rate
+            Qh[i, i] -= rate
+    Pm = np.zeros((S, Hn))
+    for i, h in enumerate(hybs):
+        for y, p in full_from(h, placements_of):
+            Pm[full_idx[y], i] += p
+    Qs = {}
+    for axis, name in ((0, "sx"), (1, "sy")):
+        M = np.zeros((S, S))
+        for i, x in enumerate(fulls):
+            for rate, y in promoter_sig_moves(W, H, n, rates, x, axis):
+                j = full_idx[y]
+                M[j, i] += rate
+                M[i, i] -= rate
+        Qs[name] = M
+    K_chi = Pm @ linalg.expm(Qh * dt) @ A
+    Ex, Ey = linalg.expm(Qs["sx"] * dt), linalg.expm(Qs["sy"] * dt)
+    p = np.zeros(S)
+    p[0] = 1.0
+    for _ in range(k_steps):
+        p = Ey @ (Ex @ (K_chi @ p))
+    return fulls, full_idx, p

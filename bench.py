@@ -271,6 +271,7 @@ def run_ours(args, rank, world, local_rank):
     g.close()
     if rank == 0 and not args.no_promoter:
         out["promoter"] = promoter_leg(args)
+        out["mixed_fidelity"] = promoter_leg(args, W.mixed_fidelity())
     if rank == 0 and not args.no_batch:
         out["batched"] = batch_leg(args)
     if rank == 0 and args.serving:
@@ -283,16 +284,18 @@ def run_ours(args, rank, world, local_rank):
     return out if rank == 0 else None
 
 
-def promoter_leg(args) -> dict:
+def promoter_leg(args, run=None) -> dict:
     """The paper's promoter Notch model (Table I rates in lattice units) on a
     64x64 tissue of 16x16-voxel cells, dt = 0.1 s, after 2 s of burn-in:
     the same timing as the main line (device-resident state, L2 flushed
-    between timed steps, CUDA events on the tissue's stream)."""
+    between timed steps, CUDA events on the tissue's stream).  With `run`
+    (the mixed-fidelity tissue) the same for that workload."""
     import torch
 
     from paper_1806_10889_gb300.tissue import Tissue
+    from paper_1806_10889_gb300.workloads import fidelity_mask
 
-    run = W.promoter()
+    run = run or W.promoter()
     g = Tissue(run.tissue)
     g.step(run.dt, 20)
     g.step(run.dt, 3)
@@ -315,8 +318,11 @@ def promoter_leg(args) -> dict:
     launch = g.launch_config()
     g.close()
     spec = run.tissue
+    mask = fidelity_mask(spec)
+    wm = int(mask.sum()) if mask is not None else 0
     return {"workload": f"promoter model, {spec.width}x{spec.height} cells of {spec.n}x{spec.n} "
-                        "voxels, dt 0.1 s, burn-in 2 s",
+                        f"voxels, dt 0.1 s, burn-in 2 s, fidelity {spec.fidelity} "
+                        f"({wm} well-mixed cells)",
             "rates": {k: v for k, v in spec.model.items() if k != "kind"},
             "events_per_s": float(ev.sum()) / (total_ms / 1e3),
             "chi_events_per_s": float(ev[0]) / (chi_ms / 1e3),
@@ -496,7 +502,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain leg")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--autotune", type=int, default=1)
-    ap.add_argument("--no-promoter", action="store_true", help="skip the promoter-model leg")
+    ap.add_argument("--no-promoter", action="store_true",
+                    help="skip the promoter-model and mixed-fidelity legs")
     ap.add_argument("--serving", type=int, default=0, help="serve the first K requests")
     ap.add_argument("--serving-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

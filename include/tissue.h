@@ -28,7 +28,8 @@
  * Arithmetic contract (exactly reproducible; the CPU oracle defines it):
  *   - Philox4x32-10, key = seed, counter = (event, step, unit,
  *     tissue_id | tag << 24) with tag 1 = chi, 2 = x-face, 3 = y-face,
- *     4 = initial counts.
+ *     4 = initial counts, 5 and 6 = the second face half-steps of Strang
+ *     splitting, 7..9 = placement of a well-mixed cell's D, N, R.
  *   - Propensities are integers in units of 2^-32 per unit time; a rate x is
  *     quantised once as round-half-even(x * 2^32).
  *   - Event times are IEEE binary64: tau = E / (A * 2^-32) with E the
@@ -128,6 +129,31 @@ int tissue_set_model(tissue* t, const tissue_model* model);
  * tissue_step returns TISSUE_E_ARG while the launch configuration selects
  * TISSUE_KERNEL_WARP, and tissue_step_noalloc does not take it. */
 int tissue_set_promoter_model(tissue* t, const tissue_promoter_model* model);
+
+/* Mixed-fidelity tissues (arXiv 1806.10889, Sec. IV: detailed modules where
+ * cells signal, coarser ones elsewhere).  host[c] (n = width*height bytes)
+ * selects the chi of cell c: 0 = the lattice RDME (default), 1 = well mixed.
+ * A well-mixed cell keeps its molecules in the same voxel layout between
+ * steps, so S and every reader see one format.  Its chi:
+ *   1. sums the cell's voxels into totals D, N, R;
+ *   2. runs the direct-method SSA on the totals over [0, dt), the cell one
+ *      compartment of V voxel volumes:
+ *      - Notch-Delta: D production V*kD / (1 + (R/(V*K))^2), N production
+ *        V*kN, decays gD*D, gN*N, gR*R, D + N -> R at (k_in/V)*D*N,
+ *        R -> D + N at k_off*R;
+ *      - promoter: transcription tD*F with F = 1 - R, unbinding kd*R,
+ *        decays d*D, d*N, binding (ka/V)*N*F;
+ *   3. places every molecule in a uniformly random voxel
+ *      v = floor(w * V / 2^32), where w is word (i mod 4) of the Philox block
+ *      (i / 4, step, cell, tissue_id | (7 + species) << 24) for the i-th
+ *      molecule of the species.  The promoter model's bound site stays on the
+ *      promoter voxel.
+ * The Hill term is binary64, left to right, rounded to nearest at each
+ * operation, then quantised.  k/V is one binary64 division, then quantised.
+ * On an error the cell is left unchanged.  Copies the array and waits for
+ * the copy.  Only the persistent chi kernel runs well-mixed cells
+ * (tissue_step returns TISSUE_E_ARG with TISSUE_KERNEL_WARP). */
+int tissue_set_cell_fidelity(tissue* t, const uint8_t* host, size_t n);
 
 /* Overwrite the state from host memory (n int32 values, exactly
  * width*height*3*V) and set the global step index (checkpoint resume).

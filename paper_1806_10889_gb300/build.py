@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libtissue.so")
-SOURCES = ["k_chi.cu", "k_chi_seg.cu", "k_chi_seg_gen.cu", "k_sig.cu", "tissue_lib.cu", "tissue_batch.cu", "tissue_noalloc.cu"]
+SOURCES = ["k_chi.cu", "k_chi_seg.cu", "k_chi_seg_gen.cu", "k_chi_wm.cu", "k_sig.cu", "tissue_lib.cu", "tissue_batch.cu", "tissue_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "--expt-relaxed-constexpr",
                      "-Xcompiler", "-fPIC,-ffp-contract=off", f"-I{INCLUDE}", f"-I{CSRC}"]

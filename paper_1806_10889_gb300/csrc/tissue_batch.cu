@@ -42,8 +42,9 @@ struct tissue_batch {
   TissueView* d_views = nullptr;
   uint2* d_items = nullptr;   // chi items of every class, then x-faces, then y-faces
   uint32_t* d_counters = nullptr;
-  size_t xface_off = 0, yface_off = 0;
+  size_t xface_off = 0, yface_off = 0, wm_off = 0;
   uint32_t n_xfaces = 0, n_yfaces = 0;
+  uint32_t n_wm = 0, wm_vmax = 0;  // well-mixed cells of all members (one launch)
   cudaGraphExec_t graph = nullptr;
   double graph_dt = 0.0;
   uint32_t steps_per_graph = 1;
@@ -53,6 +54,9 @@ struct tissue_batch {
 namespace {
 
 int chi_all(tissue_batch* b, double dt) {
+  if (b->n_wm && launch_chi_wm(b->d_views, b->d_items + b->wm_off, b->n_wm, b->wm_vmax, 0u, dt,
+                               b->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
   for (size_t c = 0; c < b->classes.size(); ++c) {
     const ClassPlan& p = b->classes[c];
     if (cudaMemsetAsync(b->d_counters + c, 0, sizeof(uint32_t), b->stream) != cudaSuccess)
@@ -119,13 +123,21 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
   // chi items by class, largest cells first; faces of both phases
   std::map<uint32_t, std::vector<uint2>, std::greater<uint32_t>> by_v;
   std::map<uint32_t, bool> gen_v;
-  std::vector<uint2> xf, yf;
+  std::vector<uint2> xf, yf, wm_items;
   for (uint32_t i = 0; i < count; ++i) {
     const tissue_desc& d = info[i].desc;
     const uint32_t V = d.n * d.n, cells = d.width * d.height;
     std::vector<uint2>& list = by_v[V];
     gen_v[V] = gen_v[V] || info[i].view.q.kind != kModelND;
-    for (uint32_t c = 0; c < cells; ++c) list.push_back(make_uint2(i, c));
+    const uint8_t* wm = info[i].wm_host;
+    for (uint32_t c = 0; c < cells; ++c) {
+      if (wm && wm[c]) {
+        wm_items.push_back(make_uint2(i, c));
+        b->wm_vmax = std::max(b->wm_vmax, V);
+      } else {
+        list.push_back(make_uint2(i, c));
+      }
+    }
     for (uint32_t c = 0; c < cells; ++c) {
       const uint32_t cx = c % d.width, cy = c / d.width;
       if (cx + 1 < d.width) xf.push_back(make_uint2(i, c));
@@ -134,6 +146,7 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
   }
   std::vector<uint2> items;
   for (auto& kv : by_v) {
+    if (kv.second.empty()) continue;  // every cell of this size is well-mixed
     ClassPlan p{};
     p.V = kv.first;
     const tissue_launch dl = default_launch(kv.first);
@@ -146,6 +159,9 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
     items.insert(items.end(), kv.second.begin(), kv.second.end());
     b->classes.push_back(p);
   }
+  b->wm_off = items.size();
+  b->n_wm = static_cast<uint32_t>(wm_items.size());
+  items.insert(items.end(), wm_items.begin(), wm_items.end());
   b->xface_off = items.size();
   b->n_xfaces = static_cast<uint32_t>(xf.size());
   items.insert(items.end(), xf.begin(), xf.end());
@@ -286,7 +302,7 @@ int tissue_batch_info(const tissue_batch* b, uint32_t* n_members, uint32_t* n_cl
   if (n_members) *n_members = static_cast<uint32_t>(b->members.size());
   if (n_classes) *n_classes = static_cast<uint32_t>(b->classes.size());
   if (n_cells) {
-    uint64_t s = 0;
+    uint64_t s = b->n_wm;
     for (const ClassPlan& p : b->classes) s += p.n_items;
     *n_cells = s;
   }

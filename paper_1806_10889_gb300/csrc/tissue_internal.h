@@ -11,6 +11,7 @@ namespace tsg {
 
 constexpr uint32_t kTagChi = 1u, kTagSx = 2u, kTagSy = 3u, kTagInit = 4u;
 constexpr uint32_t kTagSx2 = 5u, kTagSy2 = 6u;  // second half-steps of Strang splitting
+constexpr uint32_t kTagPlace = 7u;  // placement of a well-mixed cell's D (7), N (8), R (9)
 constexpr uint32_t kHillTab = 4096;  // tabulated Hill production for R < kHillTab
 constexpr int kErrOverflow = 1;
 constexpr int kErrEventIndex = 2;
@@ -34,6 +35,7 @@ struct QRates {
   uint32_t small;        // counts all below this keep every voxel total below 2^52
   uint32_t kind;         // kModelND or kModelPromoter
   uint64_t tD, kd;       // promoter: transcription by a free site, unbinding of a bound one
+  double k_in_raw, ka_raw;  // unquantised k_in / k_a: well-mixed cells use q(k / V)
 };
 
 // One tissue as the kernels see it.
@@ -49,6 +51,9 @@ struct TissueView {
   uint64_t* ev_total;   // [3][cells] events since creation
   const uint32_t* step; // device step counter
   int* err;             // device error flag (bit mask)
+  const uint8_t* wm;    // per cell: 1 = well-mixed chi; nullptr when no cell is
+  uint32_t wm_cells;    // number of well-mixed cells
+  uint32_t pad_;
 };
 
 // Launchers (enqueue on `stream`; return the launch error).
@@ -74,6 +79,10 @@ using ChiSegKernel = void (*)(const TissueView*, const uint2*, uint32_t, uint32_
 ChiSegKernel chi_seg_kernel_nd(int H, bool pre, bool qb);   // k_chi_seg.cu
 ChiSegKernel chi_seg_kernel_gen(int H, bool pre, bool qb);  // k_chi_seg_gen.cu
 uint32_t seg_bytes_for(uint32_t V, int H, bool pre);
+// Well-mixed cells (k_chi_wm.cu): one warp per (tissue, cell) item;
+// vmax_cells is the largest V among the listed cells.
+cudaError_t launch_chi_wm(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
+                          uint32_t vmax_cells, uint32_t step_off, double dt, cudaStream_t stream);
 cudaError_t launch_sig_list(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
                             int axis, uint32_t tag, double dt, cudaStream_t stream);
 cudaError_t launch_advance_list(const TissueView* d_views, uint32_t n, cudaStream_t stream);
@@ -84,6 +93,7 @@ struct TissueInfo {
   TissueView view;
   cudaStream_t stream;
   bool has_model;
+  const uint8_t* wm_host;  // per cell: 1 = well-mixed (host copy); nullptr if none
 };
 bool tissue_info(const tissue* t, TissueInfo* out);
 // The default chi launch for cells of V voxels.

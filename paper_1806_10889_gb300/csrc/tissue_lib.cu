@@ -36,6 +36,11 @@ struct tissue {
   uint32_t scheme = TISSUE_SPLIT_LIE;
   TissueView* d_view = nullptr;   // device copy of the view, for the persistent kernel
   uint32_t* d_work = nullptr;     // work-list counter of the persistent kernel
+  uint8_t* d_wm = nullptr;        // per cell: 1 = well-mixed chi
+  uint32_t wm_cells = 0;
+  std::vector<uint8_t> wm_host;   // host copy of d_wm (empty: no well-mixed cell)
+  uint2* d_lat_items = nullptr;   // (0, cell) of the lattice cells, when some are well-mixed
+  uint2* d_wm_items = nullptr;    // (0, cell) of the well-mixed cells
 };
 
 namespace {
@@ -53,7 +58,7 @@ bool desc_ok(const tissue_desc* d) {
 uint64_t cells_of(const tissue_desc* d) { return static_cast<uint64_t>(d->width) * d->height; }
 
 struct ScratchLayout {
-  size_t hill, ev_last, t_last, ev_total, step, err, view, work, total;
+  size_t hill, ev_last, t_last, ev_total, step, err, view, work, wm, lat_items, wm_items, total;
 };
 
 ScratchLayout layout(const tissue_desc* d) {
@@ -77,6 +82,12 @@ ScratchLayout layout(const tissue_desc* d) {
   o = up(o + sizeof(TissueView));
   L.work = o;
   o = up(o + sizeof(uint32_t));
+  L.wm = o;
+  o = up(o + cells);
+  L.lat_items = o;
+  o = up(o + sizeof(uint2) * cells);
+  L.wm_items = o;
+  o = up(o + sizeof(uint2) * cells);
   L.total = o;
   return L;
 }
@@ -97,6 +108,8 @@ TissueView view_of(const tissue* t) {
   v.ev_total = t->ev_total;
   v.step = t->d_step;
   v.err = t->d_err;
+  v.wm = t->wm_cells ? t->d_wm : nullptr;
+  v.wm_cells = t->wm_cells;
   return v;
 }
 
@@ -114,11 +127,17 @@ namespace {
 cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt) {
   const tissue_launch& c = t->cfg;
   if (c.kernel == TISSUE_KERNEL_PERSISTENT) {
-    cudaError_t e = cudaMemsetAsync(t->d_work, 0, sizeof(uint32_t), t->stream);
+    const uint32_t cells = t->d.width * t->d.height;
+    cudaError_t e = cudaSuccess;
+    if (t->wm_cells) {  // well-mixed cells first, then the lattice cells by list
+      e = launch_chi_wm(t->d_view, t->d_wm_items, t->wm_cells, v.V, i, dt, t->stream);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaMemsetAsync(t->d_work, 0, sizeof(uint32_t), t->stream);
     if (e != cudaSuccess) return e;
-    return launch_chi_seg(t->d_view, nullptr, t->d.width * t->d.height, t->d_work, v.V,
-                          static_cast<int>(c.lanes_per_cell), static_cast<int>(c.warps_per_block),
-                          static_cast<int>(c.blocks), i, dt,
+    return launch_chi_seg(t->d_view, t->wm_cells ? t->d_lat_items : nullptr, cells - t->wm_cells,
+                          t->d_work, v.V, static_cast<int>(c.lanes_per_cell),
+                          static_cast<int>(c.warps_per_block), static_cast<int>(c.blocks), i, dt,
                           c.smem_layout == TISSUE_LAYOUT_PREFIX, t->q.kind != kModelND,
                           t->stream);
   }
@@ -159,9 +178,10 @@ int device_error(tissue* t) {
   return h ? TISSUE_E_OVERFLOW : TISSUE_OK;
 }
 
-// The one-warp-per-cell kernel computes the Notch-Delta model only.
+// The one-warp-per-cell kernel computes lattice cells of the Notch-Delta
+// model only.
 bool launch_fits_model(const tissue* t) {
-  return t->q.kind == kModelND || t->cfg.kernel == TISSUE_KERNEL_PERSISTENT;
+  return (t->q.kind == kModelND && t->wm_cells == 0) || t->cfg.kernel == TISSUE_KERNEL_PERSISTENT;
 }
 
 bool rate_ok(double x) { return std::isfinite(x) && x >= 0.0 && x < 1048576.0; }
@@ -188,6 +208,7 @@ bool tsg::make_qrates(const double r[12], const uint64_t* hill, QRates* q) {
   q->k_in = quantise(r[9]);
   q->k_off = quantise(r[10]);
   q->k_bind = quantise(r[11]);
+  q->k_in_raw = r[9];
   for (int nn = 0; nn <= 4; ++nn) {
     q->cD[nn] = q->gD + static_cast<uint64_t>(nn) * q->hopD;
     q->cN[nn] = q->gN + static_cast<uint64_t>(nn) * q->hopN;
@@ -207,6 +228,7 @@ bool tsg::make_qrates_promoter(const double r[6], const uint64_t* hill, QRates* 
   q->kind = kModelPromoter;
   q->tD = quantise(r[0]);
   q->k_in = quantise(r[1]);    // k_a: slot 17, N + F -> R
+  q->ka_raw = r[1];
   q->kd = quantise(r[2]);
   q->k_bind = quantise(r[3]);  // k_N: Delta -> NICD across a face
   q->gD = q->gN = quantise(r[4]);
@@ -228,6 +250,7 @@ bool tsg::tissue_info(const tissue* t, TissueInfo* out) {
   out->view = view_of(t);
   out->stream = t->stream;
   out->has_model = t->has_model;
+  out->wm_host = t->wm_cells ? t->wm_host.data() : nullptr;
   return true;
 }
 
@@ -276,6 +299,9 @@ int tissue_create(const tissue_desc* d, void* dev_counts, size_t bytes, void* cu
   t->d_err = reinterpret_cast<int*>(t->scratch + L.err);
   t->d_view = reinterpret_cast<TissueView*>(t->scratch + L.view);
   t->d_work = reinterpret_cast<uint32_t*>(t->scratch + L.work);
+  t->d_wm = reinterpret_cast<uint8_t*>(t->scratch + L.wm);
+  t->d_lat_items = reinterpret_cast<uint2*>(t->scratch + L.lat_items);
+  t->d_wm_items = reinterpret_cast<uint2*>(t->scratch + L.wm_items);
   if (cudaMemsetAsync(t->scratch, 0, L.total, t->stream) != cudaSuccess) {
     cudaFree(t->scratch);
     delete t;
@@ -321,6 +347,31 @@ int tissue_set_promoter_model(tissue* t, const tissue_promoter_model* m) {
     return TISSUE_E_CUDA;
   t->has_model = true;
   return TISSUE_OK;
+}
+
+int tissue_set_cell_fidelity(tissue* t, const uint8_t* host, size_t n) {
+  if (!t || !host || n != cells_of(&t->d)) return TISSUE_E_ARG;
+  uint32_t count = 0;
+  for (size_t i = 0; i < n; ++i) {
+    if (host[i] > 1) return TISSUE_E_ARG;
+    count += host[i];
+  }
+  std::vector<uint2> lat, wm;
+  for (uint32_t c = 0; c < n; ++c) (host[c] ? wm : lat).push_back(make_uint2(0u, c));
+  if (cudaMemcpyAsync(t->d_wm, host, n, cudaMemcpyHostToDevice, t->stream) != cudaSuccess ||
+      (!lat.empty() && cudaMemcpyAsync(t->d_lat_items, lat.data(), sizeof(uint2) * lat.size(),
+                                       cudaMemcpyHostToDevice, t->stream) != cudaSuccess) ||
+      (!wm.empty() && cudaMemcpyAsync(t->d_wm_items, wm.data(), sizeof(uint2) * wm.size(),
+                                      cudaMemcpyHostToDevice, t->stream) != cudaSuccess))
+    return TISSUE_E_CUDA;
+  t->wm_cells = count;
+  if (count) t->wm_host.assign(host, host + n);
+  else t->wm_host.clear();
+  const TissueView v = view_of(t);
+  if (cudaMemcpyAsync(t->d_view, &v, sizeof(v), cudaMemcpyHostToDevice, t->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  // the host arrays (the caller's and the item lists) are released on return
+  return cudaStreamSynchronize(t->stream) == cudaSuccess ? TISSUE_OK : TISSUE_E_CUDA;
 }
 
 int tissue_write_counts(tissue* t, const int32_t* host, size_t n, uint32_t step_index) {

@@ -73,6 +73,7 @@ SIGNATURES = {
     "tissue_create": (C.c_int, [_P(Desc), C.c_void_p, C.c_size_t, C.c_void_p, _P(C.c_void_p)]),
     "tissue_set_model": (C.c_int, [C.c_void_p, _P(Model)]),
     "tissue_set_promoter_model": (C.c_int, [C.c_void_p, _P(PromoterModel)]),
+    "tissue_set_cell_fidelity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "tissue_write_counts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint32]),
     "tissue_step": (C.c_int, [C.c_void_p, C.c_double, C.c_uint32]),
     "tissue_step_timed": (C.c_int, [C.c_void_p, C.c_double, C.c_uint32, _P(C.c_double),
@@ -200,6 +201,10 @@ class Tissue:
                              C.c_void_p(self.stream.cuda_stream), C.byref(self._h))
         _check(rc, "tissue_create")
         self.set_model(model if model is not None else spec.model)
+        from .workloads import fidelity_mask
+        mask = fidelity_mask(spec)
+        if mask is not None:
+            self.set_cell_fidelity(mask)
 
     @property
     def handle(self):
@@ -216,6 +221,12 @@ class Tissue:
                    "tissue_set_promoter_model")
         else:
             _check(lib().tissue_set_model(self._h, C.byref(self._model)), "tissue_set_model")
+
+    def set_cell_fidelity(self, well_mixed) -> None:
+        """Per cell: 1 (or True) = well-mixed chi, 0 = lattice RDME."""
+        a = np.ascontiguousarray(np.asarray(well_mixed).ravel(), dtype=np.uint8)
+        _check(lib().tissue_set_cell_fidelity(self._h, a.ctypes.data_as(C.c_void_p), a.size),
+               "tissue_set_cell_fidelity")
 
     def set_launch(self, chi_warps_per_block: int):
         _check(lib().tissue_set_launch(self._h, int(chi_warps_per_block)), "tissue_set_launch")

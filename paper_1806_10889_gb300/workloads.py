@@ -61,6 +61,10 @@ class TissueSpec:
     tissue_id: int = 0
     init_lambda: tuple = (5.0, 5.0, 5.0)
     model: dict = field(default_factory=lambda: dict(ND_MODEL))
+    # chi per cell: "lattice" (every cell a voxel lattice), "well_mixed" (every
+    # cell well mixed) or "edge:K" (lattice within K cells of the tissue's
+    # edge, well mixed inside: detail where cells signal, Sec. IV)
+    fidelity: str = "lattice"
 
     @property
     def cells(self) -> int:
@@ -78,6 +82,21 @@ class TissueSpec:
         m = dict(self.model)
         m.update(kw)
         return replace(self, model=m)
+
+
+def fidelity_mask(spec: TissueSpec):
+    """uint8 per cell, 1 = well-mixed chi; None when every cell is a lattice."""
+    if spec.fidelity == "lattice":
+        return None
+    if spec.fidelity == "well_mixed":
+        return np.ones(spec.cells, dtype=np.uint8)
+    if spec.fidelity.startswith("edge:"):
+        k = int(spec.fidelity.split(":", 1)[1])
+        cx = np.arange(spec.width)[None, :]
+        cy = np.arange(spec.height)[:, None]
+        edge = np.minimum(np.minimum(cx, spec.width - 1 - cx), np.minimum(cy, spec.height - 1 - cy))
+        return (edge >= k).astype(np.uint8).ravel()
+    raise ValueError(f"unknown fidelity {spec.fidelity!r}")
 
 
 @dataclass(frozen=True)
@@ -108,6 +127,14 @@ def promoter(side: int = 64, n: int = 16, dt: float = 0.1, n_steps: int = 500) -
     spec = TissueSpec(side, side, n, seed=6, tissue_id=0, init_lambda=(0.2, 0.05, 0.0),
                       model=promoter_model(n))
     return Run(spec, dt=dt, n_steps=n_steps)
+
+
+def mixed_fidelity(side: int = 64, n: int = 16, edge: int = 8, dt: float = 0.1,
+                   n_steps: int = 500) -> Run:
+    """The promoter tissue with lattice cells within `edge` cells of the
+    tissue's edge and well-mixed cells inside (2304 of 4096 at the defaults)."""
+    r = promoter(side, n, dt, n_steps)
+    return Run(replace(r.tissue, fidelity=f"edge:{edge}"), dt=dt, n_steps=n_steps)
 
 
 def large() -> Run:

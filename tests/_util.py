@@ -13,8 +13,9 @@ SCALE = 2 ** 32
 
 
 def orc_desc(spec: TissueSpec) -> O.Desc:
+    from paper_1806_10889_gb300.workloads import fidelity_mask
     return O.Desc(spec.width, spec.height, spec.n, seed=spec.seed, tissue_id=spec.tissue_id,
-                  init_lambda=tuple(spec.init_lambda))
+                  init_lambda=tuple(spec.init_lambda), wm=fidelity_mask(spec))
 
 
 def orc_model(spec: TissueSpec):

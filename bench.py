@@ -150,7 +150,9 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
     from dataclasses import replace
-    spec = W.medium(args.dt).tissue
+    spec = {"medium": lambda: W.medium(args.dt).tissue,
+            "promoter": lambda: W.promoter().tissue,
+            "mixed": lambda: W.mixed_fidelity().tissue}[args.workload]()
     if args.side or args.n:  # profiling cases: same model and seed, other sizes
         spec = replace(spec, width=args.side or spec.width, height=args.side or spec.height,
                        n=args.n or spec.n)
@@ -228,7 +230,8 @@ def run_ours(args, rank, world, local_rank):
     chi_rate = chi_events / chi_s if chi_s > 0 else 0.0
     hbm_achieved = STATE_BYTES_PER_CELL_RW(spec.V) * spec.cells * args.steps / chi_s / 1e9
     variant = (["warp", "persistent"][launch[0]], launch[1], launch[4])
-    ipe = CHI_INST_PER_EVENT.get(variant) if not (args.side or args.n) else None
+    ipe = (CHI_INST_PER_EVENT.get(variant)
+           if not (args.side or args.n) and args.workload == "medium" else None)
     if ipe:
         ach = chi_rate * ipe / 1e9
         roofline = {"bound": "alu", "achieved": ach, "peak": ISSUE_PEAK_GINST,
@@ -245,13 +248,15 @@ def run_ours(args, rank, world, local_rank):
                     "peak_source": f"{peak_kind} hbm_gbs"}
 
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if args.workload == "medium" else f"SSA events/s, {args.workload} tissue",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_job / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
         "data": "synthetic", "impl": "ours",
-        "config": {"workload": f"{'medium' if not (args.side or args.n) else 'custom'} tissue "
-                               f"{spec.width}x{spec.height} cells of {spec.n}x{spec.n} voxels, "
-                               "Notch-Delta model",
+        "config": {"workload": f"{args.workload if not (args.side or args.n) else 'custom'} "
+                               f"tissue {spec.width}x{spec.height} cells of {spec.n}x{spec.n} "
+                               f"voxels, {'promoter' if 'kind' in spec.model else 'Notch-Delta'}"
+                               f" model, fidelity {spec.fidelity}",
                    "dt": args.dt, "burn_in_time": args.burn_in, "cells": spec.cells,
                    "voxels_per_cell": spec.V, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}",
@@ -502,6 +507,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain leg")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--workload", choices=["medium", "promoter", "mixed"], default="medium",
+                    help="main line: the medium Notch-Delta tissue (the benchmark), or the "
+                         "promoter or mixed-fidelity tissue (profiling)")
     ap.add_argument("--no-promoter", action="store_true",
                     help="skip the promoter-model and mixed-fidelity legs")
     ap.add_argument("--serving", type=int, default=0, help="serve the first K requests")

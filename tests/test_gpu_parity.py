@@ -161,43 +161,57 @@ def test_medium_config_full_tissue(config):
     _run_both(run.tissue, run.dt, 2, config=config)
 
 
-def _neighbourhood_reference(d, m, c, dt):
-    """Oracle counts of cell c after step 0 of a large tissue, computed from
-    the cells that can influence it: chi on the 3x3 block around c, the
-    x-faces of its three rows and the y-faces of c."""
+@pytest.mark.parametrize("dt", [0.01, 1.0])
+def test_medium_config_other_dt(dt):
+    """The medium tissue at the two other step lengths, whole tissue."""
+    run = W.medium(dt)
+    _run_both(run.tissue, run.dt, 2 if dt < 1.0 else 1)
+
+
+def _neighbourhood_reference(d, m, c, dt, n_steps):
+    """Oracle counts of cell c after steps 0..n_steps-1 of a large tissue,
+    computed from the cells that can influence it.  A face carries
+    influence one cell per phase along its axis, so a wrong cell at the edge
+    of a block of Chebyshev radius K reaches at most one cell further in per
+    step.  Simulating the block of radius K = n_steps around c therefore
+    leaves c exact.  Returns c's counts and its chi statistics of the last
+    step."""
     counts = np.zeros(d.cells * 3 * d.V, dtype=np.int32)
     Wd, Hd = d.width, d.height
     cx, cy = c % Wd, c // Wd
-    block = [(x, y) for y in range(cy - 1, cy + 2) for x in range(cx - 1, cx + 2)
-             if 0 <= x < Wd and 0 <= y < Hd]
-    chi_stats = {}
-    for x, y in block:
-        cc = y * Wd + x
-        O.init_cell(d, counts, cc)
-        chi_stats[cc] = O.chi_cell(d, m, counts, cc, 0, dt)
-    for y in range(cy - 1, cy + 2):
-        if not 0 <= y < Hd:
-            continue
-        for x in (cx - 1, cx):
-            if 0 <= x and x + 1 < Wd:
-                O.sig_face(d, m, counts, y * Wd + x, 0, 0, dt)
-    if cy >= 1:
-        O.sig_face(d, m, counts, c - Wd, 1, 0, dt)
-    if cy + 1 < Hd:
-        O.sig_face(d, m, counts, c, 1, 0, dt)
+    K = n_steps
+    xs = [x for x in range(cx - K, cx + K + 1) if 0 <= x < Wd]
+    ys = [y for y in range(cy - K, cy + K + 1) if 0 <= y < Hd]
+    for y in ys:
+        for x in xs:
+            O.init_cell(d, counts, y * Wd + x)
+    stats = None
+    for k in range(n_steps):
+        for y in ys:
+            for x in xs:
+                st = O.chi_cell(d, m, counts, y * Wd + x, k, dt)
+                if y * Wd + x == c:
+                    stats = st
+        for y in ys:
+            for x in xs[:-1]:
+                O.sig_face(d, m, counts, y * Wd + x, 0, k, dt)
+        for y in ys[:-1]:
+            for x in xs:
+                O.sig_face(d, m, counts, y * Wd + x, 1, k, dt)
     V = d.V
-    return counts[c * 3 * V:(c + 1) * 3 * V].copy(), chi_stats[c]
+    return counts[c * 3 * V:(c + 1) * 3 * V].copy(), stats
 
 
 def test_large_config_sampled_cells():
-    """256x256 cells of 32x32 voxels (0.8 GB of state), one step at dt = 0.1,
-    in the launch shape the benchmark times; sampled cells (corners, edges,
-    interior) checked against the oracle computed cell by cell."""
+    """256x256 cells of 32x32 voxels (0.8 GB of state), steps 0 and 1 at
+    dt = 0.1, in the launch shape the benchmark times; sampled cells
+    (corners, edges, interior) checked against the oracle computed on the
+    neighbourhood that can influence them."""
     run = W.large()
     spec = run.tissue
     d, m = orc_desc(spec), orc_model(spec)
     g = Tissue(spec)  # default launch shape, as the benchmark uses
-    g.step(run.dt, 1)
+    g.step(run.dt, 2)
     got = g.read_counts()
     gne, gtl = g.read_stats()
     g.close()
@@ -207,7 +221,7 @@ def test_large_config_sampled_cells():
               [int(x) for x in rng.integers(0, spec.cells, size=6)]
     V = spec.V
     for c in samples:
-        ref, (ne, tl) = _neighbourhood_reference(d, m, c, run.dt)
+        ref, (ne, tl) = _neighbourhood_reference(d, m, c, run.dt, 2)
         assert gne[0, c] == ne and _bits(gtl[0, c]) == _bits(tl), c
         assert np.array_equal(got[c * 3 * V:(c + 1) * 3 * V], ref), c
 

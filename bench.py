@@ -170,6 +170,11 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         g.step(args.dt, 1)
     g.sync()
+    # the state the timed steps start from, for the CPU baseline (untimed)
+    base_state, base_step = None, 0
+    if rank == 0 and not args.no_cpu_baseline and not (args.side or args.n) \
+            and args.workload == "medium":
+        base_state, base_step = g.read_counts(), g.get_step()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -282,7 +287,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and args.serving:
         out["serving"] = serving_leg(args)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args)
+        out["cpu_baseline"] = cpu_baseline(args, base_state, base_step)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -444,20 +449,26 @@ def _oracle_patch(side: int):
     return O, d, O.Model(**spec.model)
 
 
-def cpu_baseline(args, side: int = 64, steps: int = 4):
-    """The oracle, as it stands, on a bounded patch of the benchmark tissue."""
+def cpu_baseline(args, state=None, step0: int = 0, side: int = 64, budget_s: float = 10.0,
+                 max_steps: int = 30):
+    """The oracle, as it stands, on the benchmark tissue: whole-tissue steps
+    from the state the timed GPU steps start from (after the burn-in), until
+    about budget_s seconds of CPU work are done."""
     O, d, m = _oracle_patch(side)
-    counts = O.init_counts(d)
+    counts = O.init_counts(d) if state is None else np.array(state, dtype=np.int32, copy=True)
     threads = O.max_threads()
-    total = 0
+    total, steps = 0, 0
     t0 = time.perf_counter()
-    for k in range(steps):
-        ne, _ = O.step(d, m, counts, k, 1, args.dt, n_threads=threads)
+    while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < budget_s):
+        ne, _ = O.step(d, m, counts, step0 + steps, 1, args.dt, n_threads=threads)
         total += int(ne.sum())
+        steps += 1
     dt_s = time.perf_counter() - t0
+    start = "the state after the GPU burn-in" if state is not None else "the initial state"
     return {"value": total / dt_s, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{side}x{side} cells of the medium tissue (16x16 voxels), steps 0-{steps - 1} "
-                      f"from the initial state, dt {args.dt}, {total} events in {dt_s:.2f} s"}
+            "sample": f"{side}x{side} cells of the medium tissue (16x16 voxels), {steps} steps "
+                      f"from {start} (steps {step0}-{step0 + steps - 1}), dt {args.dt}, "
+                      f"{total} events in {dt_s:.2f} s"}
 
 
 def run_reference(args, rank, world):
@@ -466,10 +477,11 @@ def run_reference(args, rank, world):
     O, d, m = _oracle_patch(args.ref_side)
     counts = O.init_counts(d)
     threads = O.max_threads()
-    for k in range(args.warmup):
+    burn = int(round(args.burn_in / args.dt))  # the same untimed burn-in as the GPU arm
+    for k in range(burn + args.warmup):
         O.step(d, m, counts, k, 1, args.dt, n_threads=threads)
     total, t0 = 0, time.perf_counter()
-    for k in range(args.warmup, args.warmup + args.steps):
+    for k in range(burn + args.warmup, burn + args.warmup + args.steps):
         ne, _ = O.step(d, m, counts, k, 1, args.dt, n_threads=threads)
         total += int(ne.sum())
     el = time.perf_counter() - t0
@@ -479,9 +491,11 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": "medium tissue 64x64 cells of 16x16 voxels, Notch-Delta model",
-                       "dt": args.dt, "sample_cells": args.ref_side ** 2},
+                       "dt": args.dt, "burn_in_time": args.burn_in,
+                       "sample_cells": args.ref_side ** 2},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{args.ref_side}x{args.ref_side}-cell patch per step"},
+                             "sample": f"{args.ref_side}x{args.ref_side}-cell patch of the medium "
+                                       f"tissue per step, after {burn} burn-in steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

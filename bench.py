@@ -465,10 +465,19 @@ def cpu_baseline(args, state=None, step0: int = 0, side: int = 64, budget_s: flo
         steps += 1
     dt_s = time.perf_counter() - t0
     start = "the state after the GPU burn-in" if state is not None else "the initial state"
+    # one core: chi of the first 256 cells of the same starting state
+    one = O.init_counts(d) if state is None else np.array(state, dtype=np.int32, copy=True)
+    ev1, t1 = 0, time.perf_counter()
+    for c in range(256):
+        ev1 += O.chi_cell(d, m, one, c, step0, args.dt)[0]
+    t1 = time.perf_counter() - t1
     return {"value": total / dt_s, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{side}x{side} cells of the medium tissue (16x16 voxels), {steps} steps "
                       f"from {start} (steps {step0}-{step0 + steps - 1}), dt {args.dt}, "
-                      f"{total} events in {dt_s:.2f} s"}
+                      f"{total} events in {dt_s:.2f} s",
+            "single_core": {"value": ev1 / t1, "unit": UNIT, "cores": 1,
+                            "sample": f"chi of cells 0-255 at step {step0}, {ev1} events in "
+                                      f"{t1:.2f} s"}}
 
 
 def run_reference(args, rank, world):

@@ -301,6 +301,34 @@ int tissue_step_noalloc(const tissue_desc* desc, const tissue_model* model, int3
  * Synchronises the device. */
 int tissue_selftest_time(uint64_t n_samples, uint64_t seed, uint64_t* mismatches);
 
+/* Event trace (tests and diagnostics; the paper has no counterpart).  While
+ * a trace is on, every fired event of chi (lattice and well-mixed cells) and
+ * of both face phases is recorded, in no particular order (sort by step,
+ * kind, unit, e):
+ *   step  global step index       kind  Philox tag of the module call
+ *                                       (1 chi, 2/3 x/y faces, 5/6 their
+ *                                       Strang second halves)
+ *   unit  cell, or owner of the face  e  event index within the call
+ *   t     local time of the event in [0, dt)
+ *   site  voxel (chi lattice cells), 0 (well-mixed cells) or voxel pair (faces)
+ *   channel  channel slot 0..18 (lattice), 0..6 (well mixed) or 0/1 (faces:
+ *            0 = from the owner's side)
+ * The layout equals the CPU oracle's trace record.  tissue_trace_begin
+ * allocates room for `capacity` records (device memory) and clears the
+ * count; recording starts with the next step and uses the persistent chi
+ * kernel (tissue_step returns TISSUE_E_ARG with TISSUE_KERNEL_WARP).
+ * tissue_trace_read waits for the stream, copies min(count, capacity,
+ * host capacity) records and stores the count (which may exceed the
+ * capacity: the excess was dropped).  tissue_trace_end frees the buffer. */
+typedef struct {
+  uint32_t step, kind, unit, e;
+  double t;
+  uint32_t site, channel;
+} tissue_event;
+int tissue_trace_begin(tissue* t, size_t capacity);
+int tissue_trace_read(tissue* t, tissue_event* host, size_t capacity, size_t* n_recorded);
+int tissue_trace_end(tissue* t);
+
 /* Release library scratch (not the caller's buffer or stream). */
 void tissue_destroy(tissue* t);
 

@@ -462,6 +462,8 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
           }
         }
       }
+      if (GEN && sl == 0) trace_event(*sv, step, kTagChi, cell, e, tn, static_cast<uint32_t>(v),
+                                      static_cast<uint32_t>(ch));
       tnow = tn;
       ++e;
       if (e == 0xFFFFFFFFu) err |= kErrEventIndex;

@@ -99,6 +99,7 @@ __device__ __forceinline__ void wm_cell(const TissueView& t, const uint32_t cell
       r -= a[j];
       ++j;
     }
+    if (sl == 0) trace_event(t, step, kTagChi, cell, e, tnow, 0u, static_cast<uint32_t>(j));
     // effects on (D, N, R) of each channel
     int dD, dN, dR;
     if (pm) {

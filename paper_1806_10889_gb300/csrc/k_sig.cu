@@ -96,6 +96,7 @@ __device__ __forceinline__ void sig_face(const TissueView& t, const uint32_t c, 
     tnow = tn;
     uint64_t delta = 0;
     if (lane == L) {
+      trace_event(t, step, tag, c, e, tn, static_cast<uint32_t>(L), r1 < c0L ? 0u : 1u);
       if (r1 < c0L) {  // D(a) + N(b) -> R(b), or Delta(a) -> NICD(b)
         Da -= 1;
         Nb = pm ? Nb + 1 : Nb - 1;

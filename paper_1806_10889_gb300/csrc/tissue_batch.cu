@@ -128,7 +128,7 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
     const tissue_desc& d = info[i].desc;
     const uint32_t V = d.n * d.n, cells = d.width * d.height;
     std::vector<uint2>& list = by_v[V];
-    gen_v[V] = gen_v[V] || info[i].view.q.kind != kModelND;
+    gen_v[V] = gen_v[V] || info[i].view.q.kind != kModelND || info[i].view.trace != nullptr;
     const uint8_t* wm = info[i].wm_host;
     for (uint32_t c = 0; c < cells; ++c) {
       if (wm && wm[c]) {

@@ -38,6 +38,13 @@ struct QRates {
   double k_in_raw, ka_raw;  // unquantised k_in / k_a: well-mixed cells use q(k / V)
 };
 
+// One recorded event (tissue_event of the C ABI; the oracle's trace record).
+struct TraceRec {
+  uint32_t step, kind, unit, e;
+  double t;
+  uint32_t site, channel;
+};
+
 // One tissue as the kernels see it.
 struct TissueView {
   int32_t* counts;      // [cell][3][V]
@@ -53,8 +60,19 @@ struct TissueView {
   int* err;             // device error flag (bit mask)
   const uint8_t* wm;    // per cell: 1 = well-mixed chi; nullptr when no cell is
   uint32_t wm_cells;    // number of well-mixed cells
-  uint32_t pad_;
+  uint32_t trace_cap;   // capacity of trace (records)
+  TraceRec* trace;      // event trace (tests); nullptr when off
+  uint32_t* trace_len;  // events recorded (may exceed trace_cap)
 };
+
+// Record one event in the tissue's trace, if it has one (any order).
+__device__ __forceinline__ void trace_event(const TissueView& t, uint32_t step, uint32_t kind,
+                                            uint32_t unit, uint32_t e, double time, uint32_t site,
+                                            uint32_t channel) {
+  if (t.trace == nullptr) return;
+  const uint32_t i = atomicAdd(t.trace_len, 1u);
+  if (i < t.trace_cap) t.trace[i] = TraceRec{step, kind, unit, e, time, site, channel};
+}
 
 // Launchers (enqueue on `stream`; return the launch error).
 cudaError_t launch_hill_table(const QRates& q, uint64_t* table, cudaStream_t stream);

@@ -5,6 +5,7 @@
 // K_sig over the x-faces, then over the y-faces, on the tissue's stream.  The
 // state never leaves device memory between steps (the paper's per-module
 // input/output files become in-place reads and writes of one array).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -41,6 +42,9 @@ struct tissue {
   std::vector<uint8_t> wm_host;   // host copy of d_wm (empty: no well-mixed cell)
   uint2* d_lat_items = nullptr;   // (0, cell) of the lattice cells, when some are well-mixed
   uint2* d_wm_items = nullptr;    // (0, cell) of the well-mixed cells
+  TraceRec* d_trace = nullptr;    // event trace (tissue_trace_begin); nullptr when off
+  uint32_t* d_trace_len = nullptr;
+  uint32_t trace_cap = 0;
 };
 
 namespace {
@@ -110,6 +114,9 @@ TissueView view_of(const tissue* t) {
   v.err = t->d_err;
   v.wm = t->wm_cells ? t->d_wm : nullptr;
   v.wm_cells = t->wm_cells;
+  v.trace = t->d_trace;
+  v.trace_len = t->d_trace_len;
+  v.trace_cap = t->trace_cap;
   return v;
 }
 
@@ -138,8 +145,8 @@ cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt
     return launch_chi_seg(t->d_view, t->wm_cells ? t->d_lat_items : nullptr, cells - t->wm_cells,
                           t->d_work, v.V, static_cast<int>(c.lanes_per_cell),
                           static_cast<int>(c.warps_per_block), static_cast<int>(c.blocks), i, dt,
-                          c.smem_layout == TISSUE_LAYOUT_PREFIX, t->q.kind != kModelND,
-                          t->stream);
+                          c.smem_layout == TISSUE_LAYOUT_PREFIX,
+                          t->q.kind != kModelND || t->d_trace != nullptr, t->stream);
   }
   return launch_chi(v, i, dt, static_cast<int>(c.warps_per_block), t->stream);
 }
@@ -181,7 +188,15 @@ int device_error(tissue* t) {
 // The one-warp-per-cell kernel computes lattice cells of the Notch-Delta
 // model only.
 bool launch_fits_model(const tissue* t) {
-  return (t->q.kind == kModelND && t->wm_cells == 0) || t->cfg.kernel == TISSUE_KERNEL_PERSISTENT;
+  return (t->q.kind == kModelND && t->wm_cells == 0 && t->d_trace == nullptr) ||
+         t->cfg.kernel == TISSUE_KERNEL_PERSISTENT;
+}
+
+int upload_view(tissue* t) {
+  const TissueView v = view_of(t);
+  return cudaMemcpyAsync(t->d_view, &v, sizeof(v), cudaMemcpyHostToDevice, t->stream) == cudaSuccess
+             ? TISSUE_OK
+             : TISSUE_E_CUDA;
 }
 
 bool rate_ok(double x) { return std::isfinite(x) && x >= 0.0 && x < 1048576.0; }
@@ -536,9 +551,54 @@ int tissue_get_launch_config(const tissue* t, tissue_launch* c) {
   return TISSUE_OK;
 }
 
+int tissue_trace_begin(tissue* t, size_t capacity) {
+  if (!t || capacity == 0 || capacity > 0xFFFFFFFFull) return TISSUE_E_ARG;
+  tissue_trace_end(t);
+  if (cudaStreamSynchronize(t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  void* p = nullptr;
+  if (cudaMalloc(&p, sizeof(TraceRec) * capacity + 256) != cudaSuccess) {
+    cudaGetLastError();
+    return TISSUE_E_NOMEM;
+  }
+  t->d_trace_len = static_cast<uint32_t*>(p);
+  t->d_trace = reinterpret_cast<TraceRec*>(static_cast<unsigned char*>(p) + 256);
+  t->trace_cap = static_cast<uint32_t>(capacity);
+  if (cudaMemsetAsync(t->d_trace_len, 0, sizeof(uint32_t), t->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  return upload_view(t);
+}
+
+int tissue_trace_read(tissue* t, tissue_event* host, size_t capacity, size_t* n_recorded) {
+  static_assert(sizeof(tissue_event) == sizeof(TraceRec), "trace record layout");
+  if (!t || !n_recorded || (capacity && !host)) return TISSUE_E_ARG;
+  if (!t->d_trace) return TISSUE_E_ARG;
+  uint32_t n = 0;
+  if (cudaMemcpyAsync(&n, t->d_trace_len, sizeof(n), cudaMemcpyDeviceToHost, t->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(t->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  *n_recorded = n;
+  const size_t k = std::min<size_t>(std::min<size_t>(n, t->trace_cap), capacity);
+  if (k && cudaMemcpy(host, t->d_trace, sizeof(TraceRec) * k, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  return device_error(t);
+}
+
+int tissue_trace_end(tissue* t) {
+  if (!t) return TISSUE_E_ARG;
+  if (!t->d_trace_len) return TISSUE_OK;
+  if (cudaStreamSynchronize(t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  cudaFree(t->d_trace_len);
+  t->d_trace = nullptr;
+  t->d_trace_len = nullptr;
+  t->trace_cap = 0;
+  return upload_view(t);
+}
+
 void tissue_destroy(tissue* t) {
   if (!t) return;
   cudaStreamSynchronize(t->stream);
+  if (t->d_trace_len) cudaFree(t->d_trace_len);
   cudaFree(t->scratch);
   delete t;
 }

@@ -54,6 +54,10 @@ class PromoterModel(C.Structure):
     _fields_ = [(f, C.c_double) for f in PROMOTER_FIELDS]
 
 
+# tissue_event of the C ABI (the oracle's trace record has the same layout)
+EVENT_DTYPE = np.dtype([("step", "<u4"), ("kind", "<u4"), ("unit", "<u4"), ("e", "<u4"),
+                        ("t", "<f8"), ("site", "<u4"), ("channel", "<u4")])
+
 KERNEL_WARP, KERNEL_PERSISTENT = 0, 1
 LAYOUT_PREFIX, LAYOUT_RECOMPUTE = 0, 1
 SPLIT_LIE, SPLIT_STRANG = 0, 1
@@ -74,6 +78,9 @@ SIGNATURES = {
     "tissue_set_model": (C.c_int, [C.c_void_p, _P(Model)]),
     "tissue_set_promoter_model": (C.c_int, [C.c_void_p, _P(PromoterModel)]),
     "tissue_set_cell_fidelity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "tissue_trace_begin": (C.c_int, [C.c_void_p, C.c_size_t]),
+    "tissue_trace_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, _P(C.c_size_t)]),
+    "tissue_trace_end": (C.c_int, [C.c_void_p]),
     "tissue_write_counts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint32]),
     "tissue_step": (C.c_int, [C.c_void_p, C.c_double, C.c_uint32]),
     "tissue_step_timed": (C.c_int, [C.c_void_p, C.c_double, C.c_uint32, _P(C.c_double),
@@ -227,6 +234,29 @@ class Tissue:
         a = np.ascontiguousarray(np.asarray(well_mixed).ravel(), dtype=np.uint8)
         _check(lib().tissue_set_cell_fidelity(self._h, a.ctypes.data_as(C.c_void_p), a.size),
                "tissue_set_cell_fidelity")
+
+    def trace_begin(self, capacity: int) -> None:
+        """Record every event of the following steps (up to `capacity`)."""
+        _check(lib().tissue_trace_begin(self._h, int(capacity)), "tissue_trace_begin")
+        self._trace_cap = int(capacity)
+
+    def trace_read(self) -> np.ndarray:
+        """The recorded events, sorted by (step, kind, unit, e).  Raises if
+        more events happened than the capacity holds."""
+        n = C.c_size_t()
+        _check(lib().tissue_trace_read(self._h, None, 0, C.byref(n)), "tissue_trace_read")
+        if n.value > self._trace_cap:
+            raise RuntimeError(f"{n.value} events exceed the trace capacity {self._trace_cap}")
+        out = np.zeros(n.value, dtype=EVENT_DTYPE)
+        got = C.c_size_t()
+        _check(lib().tissue_trace_read(self._h, out.ctypes.data_as(C.c_void_p), out.size,
+                                       C.byref(got)), "tissue_trace_read")
+        if got.value != n.value:
+            raise RuntimeError("events were recorded while reading the trace")
+        return np.sort(out, order=["step", "kind", "unit", "e"])
+
+    def trace_end(self) -> None:
+        _check(lib().tissue_trace_end(self._h), "tissue_trace_end")
 
     def set_launch(self, chi_warps_per_block: int):
         _check(lib().tissue_set_launch(self._h, int(chi_warps_per_block)), "tissue_set_launch")

@@ -16,6 +16,9 @@ copied host->device before and device->host after every step.
 Multi-GPU (torchrun, N ranks): every rank advances its own replica tissue
 (tissue_id = rank); there is no data exchange (weak scaling).
 
+The serving leg (default: the first 4 requests of the serving workload,
+about a minute) reports p50/p99 latency beside the served events/s.
+
 `--impl reference` times the CPU oracle (test infrastructure, plain C with
 OpenMP) on a bounded patch of the same workload.
 """
@@ -172,7 +175,7 @@ def run_ours(args, rank, world, local_rank):
     g.sync()
     # the state the timed steps start from, for the CPU baseline (untimed)
     base_state, base_step = None, 0
-    if rank == 0 and not args.no_cpu_baseline and not (args.side or args.n) \
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not (args.side or args.n) \
             and args.workload == "medium":
         base_state, base_step = g.read_counts(), g.get_step()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
@@ -279,14 +282,14 @@ def run_ours(args, rank, world, local_rank):
         "wall_s_timed": wall,
     }
     g.close()
-    if rank == 0 and not args.no_promoter:
+    if rank == 0 and world == 1 and not args.no_promoter:
         out["promoter"] = promoter_leg(args)
         out["mixed_fidelity"] = promoter_leg(args, W.mixed_fidelity())
-    if rank == 0 and not args.no_batch:
+    if rank == 0 and world == 1 and not args.no_batch:
         out["batched"] = batch_leg(args)
-    if rank == 0 and args.serving:
+    if rank == 0 and world == 1 and args.serving:
         out["serving"] = serving_leg(args)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, base_state, base_step)
     if dist:
         dist.barrier()
@@ -535,7 +538,8 @@ def main():
                          "promoter or mixed-fidelity tissue (profiling)")
     ap.add_argument("--no-promoter", action="store_true",
                     help="skip the promoter-model and mixed-fidelity legs")
-    ap.add_argument("--serving", type=int, default=0, help="serve the first K requests")
+    ap.add_argument("--serving", type=int, default=4,
+                    help="serve the first K requests of the serving workload (0: skip)")
     ap.add_argument("--serving-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

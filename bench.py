@@ -428,6 +428,7 @@ def serving_leg(args) -> dict:
     res = srv.run(reqs)
     wall = time.perf_counter() - t0
     out = {"requests": len(reqs), "arrivals_per_s": 50.0, "budget_bytes": srv.budget,
+           "policy": f"{srv.policy} (rounds of at least {srv.fill_cells} cells)",
            "served_events_per_s": srv.device_events / wall, "wall_s": wall,
            "latency": latency_summary(res)}
     if args.serving_plain:

@@ -393,8 +393,14 @@ int tissue_write_counts(tissue* t, const int32_t* host, size_t n, uint32_t step_
   if (!t || !host) return TISSUE_E_ARG;
   const size_t want = tissue_state_bytes(&t->d) / sizeof(int32_t);
   if (n != want) return TISSUE_E_ARG;
-  for (size_t i = 0; i < n; ++i)
-    if (host[i] < 0 || host[i] > TISSUE_COUNT_MAX) return TISSUE_E_ARG;
+  // 0 <= count <= TISSUE_COUNT_MAX, as one unsigned compare (a negative count
+  // is a large unsigned value); a branch-free reduction the compiler vectorises
+  uint32_t worst = 0;
+  for (size_t i = 0; i < n; ++i) {
+    const uint32_t x = static_cast<uint32_t>(host[i]);
+    worst = x > worst ? x : worst;
+  }
+  if (worst > static_cast<uint32_t>(TISSUE_COUNT_MAX)) return TISSUE_E_ARG;
   if (cudaMemcpyAsync(t->counts, host, n * sizeof(int32_t), cudaMemcpyHostToDevice, t->stream) !=
       cudaSuccess)
     return TISSUE_E_CUDA;

@@ -10,13 +10,21 @@ in whichever slot and batch it lands.
 The server loop:
   1. admit arrived requests in arrival order while the bytes they need
      (state + library scratch of every replica) fit the budget;
-  2. rebuild the batch when its membership changed;
-  3. advance every active tissue by one chunk of steps with one batch step
-     (one persistent launch per cell-size class and step);
+  2. choose the round's requests (the scheduling policy, below) and rebuild
+     the batch when its membership changed;
+  3. advance the chosen requests' tissues by one chunk of steps with one
+     batch step (one persistent launch per cell-size class and step);
   4. retire requests whose tissues reached their step count: read the
      result back, free the memory, record the latency.
 Requests that arrive while others run join at the next chunk boundary, so
 their work overlaps on the device with the work already in flight.
+
+Policies: "srpt" (default) takes the active requests in order of least
+remaining work (cells x steps left) until the round holds at least
+`fill_cells` cells, enough to keep the device busy, and leaves the rest
+waiting; small requests then finish early instead of paying every step of
+the large ones.  "lockstep" advances every active request every round.
+The policy decides only when a tissue steps, never what a step computes.
 """
 from __future__ import annotations
 
@@ -73,7 +81,12 @@ class Server:
     """
 
     def __init__(self, budget_bytes: int, chunk_steps: int = 10, tuned: dict | None = None,
-                 keep_counts: bool = False, clock=time.perf_counter):
+                 keep_counts: bool = False, clock=time.perf_counter, policy: str = "srpt",
+                 fill_cells: int = 16384):
+        if policy not in ("srpt", "lockstep"):
+            raise ValueError(f"unknown policy {policy!r}")
+        self.policy = policy
+        self.fill_cells = int(fill_cells)
         self.budget = int(budget_bytes)
         self.chunk = int(chunk_steps)
         self.tuned = tuned
@@ -118,22 +131,23 @@ class Server:
                     if wait > 0:
                         time.sleep(min(wait, 0.05))
                 continue
-            # 2. the batch follows the active set
-            key = tuple(id(t) for a in active for t in a.tissues)
+            # 2. the round's requests; the batch follows them
+            chosen = self._choose(active)
+            key = tuple(id(t) for a in chosen for t in a.tissues)
             if key != members_key:
                 if batch is not None:
                     batch.close()
-                batch = Batch([t for a in active for t in a.tissues])
+                batch = Batch([t for a in chosen for t in a.tissues])
                 if self.tuned:
                     from .autotune import apply_batch
                     apply_batch(batch, self.tuned)
                 members_key = key
-            # 3. one chunk, bounded by the request that finishes first
-            dt = active[0].req.dt
-            k = min(self.chunk, min(a.req.n_steps - a.steps_done for a in active))
+            # 3. one chunk, bounded by the chosen request that finishes first
+            dt = chosen[0].req.dt
+            k = min(self.chunk, min(a.req.n_steps - a.steps_done for a in chosen))
             batch.step(dt, k)
             batch.sync()
-            for a in active:
+            for a in chosen:
                 a.steps_done += k
             self.peak_used = max(self.peak_used, self.used)
             # 4. retire finished requests
@@ -166,6 +180,19 @@ class Server:
             batch.close()
         torch.cuda.synchronize()
         return [results[r.index] for r in sorted(requests, key=lambda r: r.index)]
+
+    def _choose(self, active: list) -> list:
+        if self.policy == "lockstep":
+            return active
+        order = sorted(active, key=lambda a: (a.result.cells * (a.req.n_steps - a.steps_done),
+                                              a.req.index))
+        chosen, cells = [], 0
+        for a in order:
+            chosen.append(a)
+            cells += a.result.cells
+            if cells >= self.fill_cells:
+                break
+        return chosen
 
 
 def latency_summary(results: list[Result]) -> dict:

@@ -48,3 +48,18 @@ def test_budget_admission_and_rejection():
     srv2 = Server(budget_bytes=request_bytes(big) - 1, chunk_steps=2)
     out = srv2.run([big])
     assert out[0].rejected and latency_summary(out)["served"] == 0
+
+
+def test_srpt_finishes_small_requests_first_with_the_same_results():
+    """With every request arriving at once and a round sized for one
+    request, the least remaining work goes first: the small requests finish
+    before the large one, and every result equals the lockstep schedule's."""
+    reqs = [Request(0, 0.0, 4, 8, 16, 6, 0.1),   # 256 cells
+            Request(1, 0.0, 1, 2, 8, 6, 0.1),    # 4 cells
+            Request(2, 0.0, 2, 3, 8, 6, 0.1)]    # 18 cells
+    srpt = Server(budget_bytes=1 << 34, chunk_steps=2, policy="srpt", fill_cells=1).run(reqs)
+    lock = Server(budget_bytes=1 << 34, chunk_steps=2, policy="lockstep").run(reqs)
+    assert [r.digest for r in srpt] == [r.digest for r in lock]
+    assert srpt[1].done_s < srpt[2].done_s < srpt[0].done_s
+    with pytest.raises(ValueError):
+        Server(budget_bytes=1, policy="fifo")

@@ -386,18 +386,16 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
       // slot 1 (unbinding) also frees the site (R - 1), slot 17 (binding) is
       // N + F -> R, and slots 4, 13..16 and 18 have no propensity.
       const bool pm1 = GEN && pm && ch == 1, pm17 = GEN && pm && ch == 17;
-      int sp, dd, xv = v;
-      if (sl == 0) {
-        sp = ch <= 1 ? ch : ch <= 4 ? ch - 2 : hop ? hs : ch == 17 ? (pm17 ? 1 : 0) : 2;
-        dd = ch <= 1 ? 1 : -1;
-      } else if (sl == 1) {
-        sp = hop ? hs : ch == 17 ? 1 : 0;
-        dd = hop ? 1 : ch == 17 ? (pm17 ? 0 : -1) : ch == 18 ? 1 : 0;
-        if (hop) xv = u;
-      } else {
-        sp = (ch == 17 || pm1) ? 2 : 1;
-        dd = ch >= 17 ? 1 : pm1 ? -1 : 0;
-      }
+      // the three lanes' (species, change, voxel), chosen without branches
+      const int sp0 = ch <= 1 ? ch : ch <= 4 ? ch - 2 : hop ? hs : ch == 17 ? (pm17 ? 1 : 0) : 2;
+      const int dd0 = ch <= 1 ? 1 : -1;
+      const int sp1 = hop ? hs : ch == 17 ? 1 : 0;
+      const int dd1 = hop ? 1 : ch == 17 ? (pm17 ? 0 : -1) : ch == 18 ? 1 : 0;
+      const int sp2 = (ch == 17 || pm1) ? 2 : 1;
+      const int dd2 = ch >= 17 ? 1 : pm1 ? -1 : 0;
+      const int sp = sl == 0 ? sp0 : sl == 1 ? sp1 : sp2;
+      const int dd = sl == 0 ? dd0 : sl == 1 ? dd1 : dd2;
+      const int xv = (sl == 1 && hop) ? u : v;
       if (dd != 0) {
         int32_t* c = &cnt[sp * vmax + xv];
         const int nv = *c + dd;

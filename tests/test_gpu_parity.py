@@ -309,3 +309,57 @@ def test_gpu_ensemble_immigration_death_law():
     mean = 7.0 * math.exp(-gq * 15.0) + (q_rate(5.0) / gq) * (1 - math.exp(-gq * 15.0))
     p, z = poisson_gof(x, mean)
     assert p > 0.01 and abs(z) < 3, (p, z)
+
+
+def _run_from(spec, counts0, dt, n_steps, config=None):
+    """GPU and oracle from the same explicit state, compared every step."""
+    d, m = orc_desc(spec), orc_model(spec)
+    counts = counts0.copy()
+    g = Tissue(spec)
+    if config:
+        g.set_launch_config(*config)
+    g.write_counts(counts0, 0)
+    for k in range(n_steps):
+        ne, tl = O.step(d, m, counts, k, 1, dt)
+        g.step(dt, 1)
+        _compare_step(g, d, counts, ne, tl, f"{spec} step {k}")
+    g.close()
+    return counts
+
+
+@pytest.mark.parametrize("config", [None, (T.KERNEL_WARP, 32, 4, 0),
+                                    (T.KERNEL_PERSISTENT, 32, 2, 0, T.LAYOUT_PREFIX),
+                                    (T.KERNEL_PERSISTENT, 8, 4, 0, T.LAYOUT_RECOMPUTE)])
+def test_empty_tissue_fires_nothing(config):
+    """No molecules and no production: total propensity 0 everywhere, so
+    every module call ends at once with no event and t_last = 0."""
+    spec = TissueSpec(3, 2, 8, seed=5).with_model(kD=0.0, kN=0.0)
+    zero = np.zeros(spec.state_ints, dtype=np.int32)
+    out = _run_from(spec, zero, 0.1, 2, config)
+    assert not out.any()
+
+
+@pytest.mark.parametrize("config", [None, (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_PREFIX),
+                                    (T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE)])
+def test_counts_at_the_maximum(config):
+    """Voxels holding the largest allowed count (2^30 - 1) with rates small
+    enough to stay below the propensity limit: the exactly checked
+    large-count path, bit for bit."""
+    # k_in > 0 lowers the bound below which counts take the unchecked fast
+    # path (2^25 here), so these voxels take the checked one; no voxel holds
+    # both D and N, so no total comes near 2^52
+    spec = TissueSpec(2, 2, 4, seed=6).with_model(kD=0.0, kN=0.0, gD=1e-6, gN=2e-6, gR=0.0,
+                                                  hopD=0.0, hopN=0.0, hopR=0.0, k_bind=0.0,
+                                                  k_in=1e-9)
+    x = np.zeros(spec.state_ints, dtype=np.int32).reshape(spec.cells, 3, spec.V)
+    x[:, 0, 3] = (1 << 30) - 1
+    x[1, 1, 0] = (1 << 30) - 1
+    x[2, 0, :] = 1000
+    out = _run_from(spec, x.ravel(), 0.5, 2, config).reshape(spec.cells, 3, spec.V)
+    assert out[:, 0, 3].min() < (1 << 30) - 1  # decay happened
+
+
+def test_tiny_step_length():
+    """dt = 1e-9: almost every call ends before its first event."""
+    run = W.tiny()
+    _run_both(run.tissue, 1e-9, 3)

@@ -329,6 +329,12 @@ int tissue_trace_begin(tissue* t, size_t capacity);
 int tissue_trace_read(tissue* t, tissue_event* host, size_t capacity, size_t* n_recorded);
 int tissue_trace_end(tissue* t);
 
+/* Host-side fault injection for tests: the next n device allocations the
+ * library makes (tissue_create, tissue_batch_create, tissue_trace_begin)
+ * fail as an out-of-memory cudaMalloc would (TISSUE_E_NOMEM), without
+ * touching the GPU.  n = 0 disarms it. */
+int tissue_debug_fail_allocs(uint32_t n);
+
 /* Release library scratch (not the caller's buffer or stream). */
 void tissue_destroy(tissue* t);
 

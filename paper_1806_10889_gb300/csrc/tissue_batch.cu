@@ -172,7 +172,7 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
   const size_t views_bytes = (sizeof(TissueView) * count + 255) & ~static_cast<size_t>(255);
   const size_t items_bytes = (sizeof(uint2) * items.size() + 255) & ~static_cast<size_t>(255);
   const size_t total = views_bytes + items_bytes + sizeof(uint32_t) * b->classes.size();
-  if (cudaMalloc(&b->dmem, total) != cudaSuccess) {
+  if (lib_malloc(reinterpret_cast<void**>(&b->dmem), total) != cudaSuccess) {
     cudaGetLastError();
     delete b;
     return TISSUE_E_NOMEM;
@@ -227,6 +227,7 @@ int tissue_batch_set_class_launch(tissue_batch* b, uint32_t V, uint32_t lanes_pe
 }
 
 int tissue_batch_step(tissue_batch* b, double dt, uint32_t n_steps) {
+  NvtxRange range("tissue_batch_step");
   if (!b) return TISSUE_E_ARG;
   if (!(dt > 0.0) || !std::isfinite(dt)) return TISSUE_E_ARG;
   if (n_steps == 0) return TISSUE_OK;

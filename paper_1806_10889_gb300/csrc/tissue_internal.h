@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libtissue.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "tissue.h"
 
@@ -73,6 +74,20 @@ __device__ __forceinline__ void trace_event(const TissueView& t, uint32_t step, 
   const uint32_t i = atomicAdd(t.trace_len, 1u);
   if (i < t.trace_cap) t.trace[i] = TraceRec{step, kind, unit, e, time, site, channel};
 }
+
+// NVTX range over a host-side library call (seen by profilers; no cost
+// without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Device allocation by the library: cudaMalloc, unless a test armed the
+// host-side fault injector (tissue_debug_fail_allocs), in which case it
+// fails as an out-of-memory cudaMalloc would, touching no GPU state.
+cudaError_t lib_malloc(void** p, size_t bytes);
 
 // Launchers (enqueue on `stream`; return the launch error).
 cudaError_t launch_hill_table(const QRates& q, uint64_t* table, cudaStream_t stream);

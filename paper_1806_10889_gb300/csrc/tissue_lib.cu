@@ -6,6 +6,7 @@
 // state never leaves device memory between steps (the paper's per-module
 // input/output files become in-place reads and writes of one array).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -121,6 +122,21 @@ TissueView view_of(const tissue* t) {
 }
 
 }  // namespace
+
+namespace {
+std::atomic<uint32_t> g_fail_allocs{0};
+}  // namespace
+
+cudaError_t tsg::lib_malloc(void** p, size_t bytes) {
+  uint32_t n = g_fail_allocs.load();
+  while (n > 0) {
+    if (g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
 
 tissue_launch tsg::default_launch(uint32_t V) {
   if (V <= 64) return tissue_launch{TISSUE_KERNEL_PERSISTENT, 8, 4, 0, TISSUE_LAYOUT_PREFIX};
@@ -285,6 +301,7 @@ size_t tissue_scratch_bytes(const tissue_desc* d) {
 
 int tissue_create(const tissue_desc* d, void* dev_counts, size_t bytes, void* cuda_stream,
                   tissue** out) {
+  NvtxRange range("tissue_create");
   if (!out) return TISSUE_E_ARG;
   *out = nullptr;
   if (!desc_ok(d) || !dev_counts) return TISSUE_E_ARG;
@@ -301,7 +318,7 @@ int tissue_create(const tissue_desc* d, void* dev_counts, size_t bytes, void* cu
   // above.
   t->cfg = default_launch(d->n * d->n);
   const ScratchLayout L = layout(d);
-  if (cudaMalloc(&t->scratch, L.total) != cudaSuccess) {
+  if (lib_malloc(reinterpret_cast<void**>(&t->scratch), L.total) != cudaSuccess) {
     cudaGetLastError();
     delete t;
     return TISSUE_E_NOMEM;
@@ -390,6 +407,7 @@ int tissue_set_cell_fidelity(tissue* t, const uint8_t* host, size_t n) {
 }
 
 int tissue_write_counts(tissue* t, const int32_t* host, size_t n, uint32_t step_index) {
+  NvtxRange range("tissue_write_counts");
   if (!t || !host) return TISSUE_E_ARG;
   const size_t want = tissue_state_bytes(&t->d) / sizeof(int32_t);
   if (n != want) return TISSUE_E_ARG;
@@ -414,6 +432,7 @@ int tissue_write_counts(tissue* t, const int32_t* host, size_t n, uint32_t step_
 }
 
 int tissue_step(tissue* t, double dt, uint32_t n_steps) {
+  NvtxRange range("tissue_step");
   if (!t) return TISSUE_E_ARG;
   if (!t->has_model) return TISSUE_E_NOMODEL;
   if (!(dt > 0.0) || !std::isfinite(dt) || !launch_fits_model(t)) return TISSUE_E_ARG;
@@ -429,6 +448,7 @@ int tissue_step(tissue* t, double dt, uint32_t n_steps) {
 }
 
 int tissue_step_timed(tissue* t, double dt, uint32_t n_steps, double* ms_chi, double* ms_sig) {
+  NvtxRange range("tissue_step_timed");
   if (!t) return TISSUE_E_ARG;
   if (!t->has_model) return TISSUE_E_NOMODEL;
   if (!(dt > 0.0) || !std::isfinite(dt) || !launch_fits_model(t)) return TISSUE_E_ARG;
@@ -472,6 +492,7 @@ int tissue_set_splitting(tissue* t, uint32_t scheme) {
 }
 
 int tissue_read_counts(tissue* t, int32_t* host, size_t n) {
+  NvtxRange range("tissue_read_counts");
   if (!t || !host) return TISSUE_E_ARG;
   if (n != tissue_state_bytes(&t->d) / sizeof(int32_t)) return TISSUE_E_ARG;
   if (cudaMemcpyAsync(host, t->counts, n * sizeof(int32_t), cudaMemcpyDeviceToHost, t->stream) !=
@@ -562,7 +583,7 @@ int tissue_trace_begin(tissue* t, size_t capacity) {
   tissue_trace_end(t);
   if (cudaStreamSynchronize(t->stream) != cudaSuccess) return TISSUE_E_CUDA;
   void* p = nullptr;
-  if (cudaMalloc(&p, sizeof(TraceRec) * capacity + 256) != cudaSuccess) {
+  if (lib_malloc(&p, sizeof(TraceRec) * capacity + 256) != cudaSuccess) {
     cudaGetLastError();
     return TISSUE_E_NOMEM;
   }
@@ -625,6 +646,11 @@ int tissue_selftest_time(uint64_t n_samples, uint64_t seed, uint64_t* mismatches
   cudaFree(d);
   *mismatches = h;
   return rc;
+}
+
+int tissue_debug_fail_allocs(uint32_t n) {
+  g_fail_allocs.store(n);
+  return TISSUE_OK;
 }
 
 const char* tissue_strerror(int code) {

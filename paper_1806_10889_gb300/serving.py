@@ -29,6 +29,7 @@ The policy decides only when a tissue steps, never what a step computes.
 from __future__ import annotations
 
 import hashlib
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -50,6 +51,7 @@ class Result:
     digest: str = ""
     counts: list = field(default_factory=list)
     rejected: bool = False
+    cancelled: bool = False
 
     @property
     def latency_s(self) -> float:
@@ -95,8 +97,24 @@ class Server:
         self.used = 0
         self.peak_used = 0
         self.device_events = 0
+        self._cancel: set = set()
+        self._cancel_lock = threading.Lock()
 
-    def run(self, requests: list[Request], time_scale: float = 1.0) -> list[Result]:
+    def cancel(self, index: int) -> None:
+        """Cancel request `index` (safe from any thread): a pending request
+        is dropped; an active one is stopped at the next chunk boundary and
+        its memory freed.  Its result is marked cancelled and has no digest."""
+        with self._cancel_lock:
+            self._cancel.add(int(index))
+
+    def _take_cancelled(self) -> set:
+        with self._cancel_lock:
+            return set(self._cancel)
+
+    def run(self, requests: list[Request], time_scale: float = 1.0,
+            on_round=None) -> list[Result]:
+        """Serve `requests`; on_round(server, indices), if given, is called
+        after every round with the indices of the requests it advanced."""
         import torch
         if len({r.dt for r in requests}) > 1:
             raise ValueError("one server run serves requests of a single dt")
@@ -108,6 +126,26 @@ class Server:
         t0 = self.clock()
         while pending or active:
             now = self.clock() - t0
+            # 0. cancellations: drop pending requests, stop active ones
+            cancelled = self._take_cancelled()
+            if cancelled:
+                for r in [r for r in pending if r.index in cancelled]:
+                    pending.remove(r)
+                    results[r.index].cancelled = True
+                keep = []
+                for a in active:
+                    if a.req.index not in cancelled:
+                        keep.append(a)
+                        continue
+                    if batch is not None:
+                        batch.close()
+                        batch, members_key = None, None
+                    for t in a.tissues:
+                        t.close()
+                    self.used -= a.nbytes
+                    a.result.cancelled = True
+                    a.result.done_s = now
+                active = keep
             # 1. admission, arrival order
             while pending and pending[0].arrival_s * time_scale <= now:
                 req = pending[0]
@@ -150,6 +188,8 @@ class Server:
             for a in chosen:
                 a.steps_done += k
             self.peak_used = max(self.peak_used, self.used)
+            if on_round is not None:
+                on_round(self, [a.req.index for a in chosen])
             # 4. retire finished requests
             now = self.clock() - t0
             still = []
@@ -196,9 +236,10 @@ class Server:
 
 
 def latency_summary(results: list[Result]) -> dict:
-    lat = np.array([r.latency_s for r in results if not r.rejected])
+    lat = np.array([r.latency_s for r in results if not (r.rejected or r.cancelled)])
     if lat.size == 0:
         return {"p50_s": None, "p99_s": None, "served": 0}
     return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_s": float(lat.mean()), "served": int(lat.size),
-            "rejected": int(sum(r.rejected for r in results))}
+            "rejected": int(sum(r.rejected for r in results)),
+            "cancelled": int(sum(r.cancelled for r in results))}

@@ -81,6 +81,7 @@ SIGNATURES = {
     "tissue_trace_begin": (C.c_int, [C.c_void_p, C.c_size_t]),
     "tissue_trace_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, _P(C.c_size_t)]),
     "tissue_trace_end": (C.c_int, [C.c_void_p]),
+    "tissue_debug_fail_allocs": (C.c_int, [C.c_uint32]),
     "tissue_write_counts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_uint32]),
     "tissue_step": (C.c_int, [C.c_void_p, C.c_double, C.c_uint32]),
     "tissue_step_timed": (C.c_int, [C.c_void_p, C.c_double, C.c_uint32, _P(C.c_double),
@@ -171,6 +172,12 @@ def scratch_bytes(spec: TissueSpec) -> int:
 def _check(rc: int, what: str):
     if rc != OK:
         raise TissueError(rc, what)
+
+
+def debug_fail_allocs(n: int) -> None:
+    """Make the library's next n device allocations fail as out-of-memory
+    (host-side fault injection for tests; 0 disarms)."""
+    _check(lib().tissue_debug_fail_allocs(int(n)), "tissue_debug_fail_allocs")
 
 
 def selftest_time(n_samples: int, seed: int = 1) -> int:

@@ -52,3 +52,19 @@ def test_create_rejects_bad_arguments_without_touching_the_device():
     d.n = 33
     assert L.tissue_create(C.byref(d), C.c_void_p(0x1000), 1 << 20, None, C.byref(h)) == T.E_ARG
     assert L.tissue_step(None, 0.1, 1) == T.E_ARG
+
+
+def test_injected_allocation_failure_is_reported_without_a_device():
+    """Host-side fault injection: the library's next device allocation fails
+    as an out-of-memory cudaMalloc would.  tissue_create reports
+    TISSUE_E_NOMEM and returns no handle; nothing reaches the GPU."""
+    L = T.lib()
+    d = T.desc_of(TissueSpec(2, 2, 8, seed=1))
+    h = C.c_void_p(0x1234)
+    T.debug_fail_allocs(1)
+    try:
+        rc = L.tissue_create(C.byref(d), C.c_void_p(0x1000), 1 << 20, None, C.byref(h))
+    finally:
+        T.debug_fail_allocs(0)
+    assert rc == T.E_NOMEM and not h.value
+    assert L.tissue_strerror(T.E_NOMEM) == b"out of device memory"

@@ -63,3 +63,26 @@ def test_srpt_finishes_small_requests_first_with_the_same_results():
     assert srpt[1].done_s < srpt[2].done_s < srpt[0].done_s
     with pytest.raises(ValueError):
         Server(budget_bytes=1, policy="fifo")
+
+
+def test_cancel_pending_and_active_requests():
+    """Cancelling frees the request's memory and leaves every other result
+    as it would be alone."""
+    reqs = [Request(0, 0.0, 2, 4, 16, 8, 0.1), Request(1, 0.0, 1, 3, 8, 8, 0.1),
+            Request(2, 0.0, 1, 2, 8, 8, 0.1)]
+    srv = Server(budget_bytes=1 << 34, chunk_steps=2, policy="lockstep")
+    srv.cancel(2)  # still pending when the run starts
+
+    def after_round(server, indices):
+        if 0 in indices:
+            server.cancel(0)  # active: stopped at the next chunk boundary
+
+    res = srv.run(reqs, on_round=after_round)
+    assert res[0].cancelled and not res[0].digest
+    assert res[2].cancelled and not res[2].digest
+    assert not res[1].cancelled and res[1].digest
+    alone = Server(budget_bytes=1 << 34, chunk_steps=3).run([reqs[1]])[0]
+    assert alone.digest == res[1].digest
+    assert srv.used == 0
+    s = latency_summary(res)
+    assert s["served"] == 1 and s["cancelled"] == 2

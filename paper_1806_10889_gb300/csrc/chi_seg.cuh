@@ -320,20 +320,28 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     uint64_t r2 = r1 - (i2 > 0 ? pp : 0ull);
     int v = vb + (i2 << qb);
     bool bad_q = false;
-    if (PRE && QB && qb > 0) {
-      // the voxel inside lane i2's run of Q voxels: a short uniform scan
+    if (PRE && QB) {
+      // the voxel inside lane i2's run of Q = 2^qb voxels: the segment's
+      // lanes read H of the run's prefix entries at a time and one ballot
+      // finds the first that exceeds r1 (Q = 1 re-finds lane i2's voxel).
+      // Every lane of the warp runs the same trip count (the warp's largest
+      // Q), so the collectives inside stay converged.
+      const int qmax = static_cast<int>(__reduce_max_sync(kFull, 1u << qb));
       uint64_t before_v = i2 > 0 ? pp : 0ull;
       int pick = -1;
-      for (int kq = 0; kq < (1 << qb); ++kq) {
-        const int idx = v + kq;
-        if (pick < 0 && idx < s.V) {
-          const uint64_t x = pre[idx];
-          if (r1 < x) {
-            pick = idx;
-            r2 = r1 - before_v;
-          }
-          before_v = x;
+      for (int k0 = 0; k0 < qmax; k0 += H) {
+        const int idx = v + k0 + sl;
+        const bool in = k0 + sl < (1 << qb) && idx < s.V;
+        const uint64_t x = in ? pre[idx] : ~0ull;
+        const unsigned mq = (__ballot_sync(kFull, in && r1 < x) >> (seg * H)) & kSegBits;
+        const int kq = mq ? __ffs(mq) - 1 : 0;
+        const uint64_t xprev = __shfl_sync(kFull, x, kq > 0 ? kq - 1 : 0, H);
+        const uint64_t xlast = __shfl_sync(kFull, x, H - 1, H);
+        if (pick < 0 && mq) {
+          pick = v + k0 + kq;
+          r2 = r1 - (kq > 0 ? xprev : before_v);
         }
+        before_v = xlast;
       }
       bad_q = pick < 0;
       v = pick < 0 ? v : pick;

@@ -63,6 +63,7 @@ extern "C" {
 #define TISSUE_E_TIMEOUT (-6)  /* a bounded device wait gave up */
 #define TISSUE_E_BUDGET (-7)   /* admission refused: memory budget exceeded */
 #define TISSUE_E_STATE (-9)    /* promoter model: a voxel holds more bound sites than sites */
+#define TISSUE_E_BOUNDS (-10)  /* checked build only: a kernel caught an index out of range */
 
 #define TISSUE_COUNT_MAX ((1 << 30) - 1)
 

@@ -77,10 +77,11 @@ __device__ __forceinline__ uint32_t dir_mask(int v, const Seg& s) {
 template <bool GEN>
 __device__ __forceinline__ uint64_t seg_voxel_total(const int32_t* cnt, int vmax, int v,
                                                     const Seg& s, const QRates& q, bool pm,
-                                                    bool& ovf) {
-  const uint32_t D = static_cast<uint32_t>(cnt[v]);
-  const uint32_t N = static_cast<uint32_t>(cnt[vmax + v]);
-  const uint32_t R = static_cast<uint32_t>(cnt[2 * vmax + v]);
+                                                    bool& ovf, bool& oob) {
+  const int vi = static_cast<int>(TSG_IDX(v, vmax, oob));
+  const uint32_t D = static_cast<uint32_t>(cnt[vi]);
+  const uint32_t N = static_cast<uint32_t>(cnt[vmax + vi]);
+  const uint32_t R = static_cast<uint32_t>(cnt[2 * vmax + vi]);
   const int nn = __popc(dir_mask(v, s));
   uint64_t c0, c1, X;
   voxel_terms<GEN>(pm, q, v, s, D, N, R, true, c0, c1, X);
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
 
   static_assert(PRE || !QB, "the recompute layout needs B <= H");
   bool have = false, done = false, pm = false;
+  bool oob = false;  // checked build: an index out of range (see TSG_IDX)
   Seg s{0, 2, 1, 0, 1, 0, 0};
   uint32_t cell = 0, step = 0, word3 = 0, key0 = 0, key1 = 0, e = 0, e0 = 0;
   uint64_t A = 0, P = 0, Em = 0, Rb = 0, Em2 = 0, Rb2 = 0;
@@ -192,53 +194,62 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
         while ((H << s.qb) < s.B) ++s.qb;
         s.centre = (s.n >> 1) * s.n + (s.n >> 1);
         pm = GEN && sv->q.kind == kModelPromoter;
-        g = sv->counts + static_cast<size_t>(cell) * 3 * s.V;
-        if ((s.V & 3) == 0) {
-          const int V4 = s.V >> 2;
-          for (int sp = 0; sp < 3; ++sp) {
-            const int4* a = reinterpret_cast<const int4*>(g + sp * s.V);
-            int4* b = reinterpret_cast<int4*>(cnt + sp * vmax);
-            for (int i = sl; i < V4; i += H) b[i] = a[i];
-          }
+        const bool skip = kChecked && (s.V > vmax || cell >= sv->width * sv->height);
+        if (skip) {
+          // the cell does not fit this launch's shared memory, or is not in
+          // its tissue: report it; the segment stays idle this pass and takes
+          // the next item on the next one
+          if (sl == 0) atomicOr(sv->err, kErrBounds);
+          __syncwarp(segmask);
         } else {
-          for (int sp = 0; sp < 3; ++sp)
-            for (int i = sl; i < s.V; i += H) cnt[sp * vmax + i] = g[sp * s.V + i];
-        }
-        __syncwarp(segmask);
-        step = *sv->step + step_off;
-        key0 = static_cast<uint32_t>(sv->seed);
-        key1 = static_cast<uint32_t>(sv->seed >> 32);
-        word3 = sv->tissue_id | (kTagChi << 24);
-        bool ovf = false, bad_state = false;
-        const bool bad_qb = !QB && s.qb > 0;  // the launcher never lets this happen
-        uint64_t S = 0;
-        for (int i = 0; i < s.B; ++i) {
-          const int v = (sl << s.lb) + i;
-          if (v < s.V) {
-            // promoter model: bound sites never exceed the voxel's sites
-            if (pm && cnt[2 * vmax + v] > static_cast<int32_t>(v == s.centre)) bad_state = true;
-            S += seg_voxel_total<GEN>(cnt, vmax, v, s, sv->q, pm, ovf);
-            if (PRE) pre[v] = S;
+          g = sv->counts + static_cast<size_t>(cell) * 3 * s.V;
+          if ((s.V & 3) == 0) {
+            const int V4 = s.V >> 2;
+            for (int sp = 0; sp < 3; ++sp) {
+              const int4* a = reinterpret_cast<const int4*>(g + sp * s.V);
+              int4* b = reinterpret_cast<int4*>(cnt + sp * vmax);
+              for (int i = sl; i < V4; i += H) b[i] = a[i];
+            }
+          } else {
+            for (int sp = 0; sp < 3; ++sp)
+              for (int i = sl; i < s.V; i += H) cnt[sp * vmax + i] = g[sp * s.V + i];
           }
+          __syncwarp(segmask);
+          step = *sv->step + step_off;
+          key0 = static_cast<uint32_t>(sv->seed);
+          key1 = static_cast<uint32_t>(sv->seed >> 32);
+          word3 = sv->tissue_id | (kTagChi << 24);
+          bool ovf = false, bad_state = false;
+          const bool bad_qb = !QB && s.qb > 0;  // the launcher never lets this happen
+          uint64_t S = 0;
+          for (int i = 0; i < s.B; ++i) {
+            const int v = (sl << s.lb) + i;
+            if (v < s.V) {
+              // promoter model: bound sites never exceed the voxel's sites
+              if (pm && cnt[2 * vmax + v] > static_cast<int32_t>(v == s.centre)) bad_state = true;
+              S += seg_voxel_total<GEN>(cnt, vmax, v, s, sv->q, pm, ovf, oob);
+              if (PRE) pre[TSG_IDX(v, vmax, oob)] = S;
+            }
+          }
+          P = S;
+  #pragma unroll
+          for (int o = 1; o < H; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(segmask, P, o, H);
+            if (sl >= o) P += y;
+          }
+          A = __shfl_sync(segmask, P, H - 1, H);
+          tnow = 0.0;
+          e = 0;
+          e0 = 0;
+          draw_event(e0 + sl, step, cell, word3, key0, key1, Em, Ek, Rb);
+          next_ok = false;
+          err = bad_qb                         ? kErrInternal
+                : __any_sync(segmask, bad_state) ? kErrState
+                : __any_sync(segmask, ovf)       ? kErrOverflow
+                                                 : 0;
+          have = true;
+          __syncwarp(segmask);
         }
-        P = S;
-#pragma unroll
-        for (int o = 1; o < H; o <<= 1) {
-          const uint64_t y = __shfl_up_sync(segmask, P, o, H);
-          if (sl >= o) P += y;
-        }
-        A = __shfl_sync(segmask, P, H - 1, H);
-        tnow = 0.0;
-        e = 0;
-        e0 = 0;
-        draw_event(e0 + sl, step, cell, word3, key0, key1, Em, Ek, Rb);
-        next_ok = false;
-        err = bad_qb                         ? kErrInternal
-              : __any_sync(segmask, bad_state) ? kErrState
-              : __any_sync(segmask, ovf)       ? kErrOverflow
-                                               : 0;
-        have = true;
-        __syncwarp(segmask);
       }
     }
     if (__all_sync(kFull, done)) break;
@@ -301,12 +312,14 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     if (PRE) {
       // lane sl covers voxels vb + sl*Q .. + Q-1 of the block (Q = 2^qb; 1 if B <= H)
       const int q0 = vb + (sl << qb);
-      if ((sl << qb) < s.B && q0 < s.V) pv = pre[min(q0 + (1 << qb) - 1, s.V - 1)];
+      if ((sl << qb) < s.B && q0 < s.V)
+        pv = pre[TSG_IDX(min(q0 + (1 << qb) - 1, s.V - 1), vmax, oob)];
     } else {
       // the block's voxel propensities, recomputed, then their running sum
       bool unused = false;
       const bool mine = act && sl < s.B && vb + sl < s.V;
-      uint64_t cx = mine ? seg_voxel_total<GEN>(cnt, vmax, vb + sl, s, q, pm, unused) : 0ull;
+      uint64_t cx =
+          mine ? seg_voxel_total<GEN>(cnt, vmax, vb + sl, s, q, pm, unused, oob) : 0ull;
 #pragma unroll
       for (int o = 1; o < H; o <<= 1) {
         const uint64_t y = __shfl_up_sync(kFull, cx, o, H);
@@ -332,7 +345,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
       for (int k0 = 0; k0 < qmax; k0 += H) {
         const int idx = v + k0 + sl;
         const bool in = k0 + sl < (1 << qb) && idx < s.V;
-        const uint64_t x = in ? pre[idx] : ~0ull;
+        const uint64_t x = in ? pre[TSG_IDX(idx, vmax, oob)] : ~0ull;
         const unsigned mq = (__ballot_sync(kFull, in && r1 < x) >> (seg * H)) & kSegBits;
         const int kq = mq ? __ffs(mq) - 1 : 0;
         const uint64_t xprev = __shfl_sync(kFull, x, kq > 0 ? kq - 1 : 0, H);
@@ -351,9 +364,10 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     if (bad1 || v >= s.V) v = 0;
 
     // channel: closed-form running sums
-    const uint32_t D = static_cast<uint32_t>(cnt[v]);
-    const uint32_t N = static_cast<uint32_t>(cnt[vmax + v]);
-    const uint32_t R = static_cast<uint32_t>(cnt[2 * vmax + v]);
+    const int vi = static_cast<int>(TSG_IDX(v, vmax, oob));
+    const uint32_t D = static_cast<uint32_t>(cnt[vi]);
+    const uint32_t N = static_cast<uint32_t>(cnt[vmax + vi]);
+    const uint32_t R = static_cast<uint32_t>(cnt[2 * vmax + vi]);
     const uint32_t hm = dir_mask(v, s);
     uint64_t c0, c1, X;
     voxel_terms<GEN>(pm, q, v, s, D, N, R, act, c0, c1, X);
@@ -387,7 +401,9 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     if (u >= s.V) u = -1;
     const bool fire_ok = fire && !bad_u;
     uint64_t a_old_u = 0;
-    if (PRE && u >= 0) a_old_u = pre[u] - ((u & (s.B - 1)) ? pre[u - 1] : 0ull);
+    if (PRE && u >= 0)
+      a_old_u = pre[TSG_IDX(u, vmax, oob)] -
+                ((u & (s.B - 1)) ? pre[TSG_IDX(u - 1, vmax, oob)] : 0ull);
     __syncwarp();
     if (fire_ok && sl < 3) {
       // Notch-Delta: slot 17 is D + N -> R, 18 is R -> D + N.  Promoter:
@@ -405,7 +421,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
       const int dd = sl == 0 ? dd0 : sl == 1 ? dd1 : dd2;
       const int xv = (sl == 1 && hop) ? u : v;
       if (dd != 0) {
-        int32_t* c = &cnt[sp * vmax + xv];
+        int32_t* c = &cnt[TSG_IDX(sp * vmax + xv, 3 * vmax, oob)];
         const int nv = *c + dd;
         *c = nv;
         if (nv > kCountMax) err |= kErrOverflow;
@@ -416,19 +432,20 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     uint64_t dv, du;
     if (PRE) {
       const uint64_t a_new =
-          act ? seg_voxel_total<GEN>(cnt, vmax, (sl == 1 && u >= 0) ? u : v, s, q, pm, ovf)
+          act ? seg_voxel_total<GEN>(cnt, vmax, (sl == 1 && u >= 0) ? u : v, s, q, pm, ovf, oob)
               : 0ull;
       dv = __shfl_sync(kFull, a_new, 0, H) - a_old_v;
       du = __shfl_sync(kFull, a_new, 1, H) - a_old_u;
     } else {
-      dv = (act ? seg_voxel_total<GEN>(cnt, vmax, v, s, q, pm, ovf) : 0ull) - a_old_v;
+      dv = (act ? seg_voxel_total<GEN>(cnt, vmax, v, s, q, pm, ovf, oob) : 0ull) - a_old_v;
       // one molecule of species hs arrived at u: the change of u's total in
       // closed form (the total is affine in D and N apart from k_in X)
       du = 0;
       if (act && u >= 0) {
-        const uint32_t Du = static_cast<uint32_t>(cnt[u]);
-        const uint32_t Nu = static_cast<uint32_t>(cnt[vmax + u]);
-        const uint32_t Ru = static_cast<uint32_t>(cnt[2 * vmax + u]);
+        const int ui = static_cast<int>(TSG_IDX(u, vmax, oob));
+        const uint32_t Du = static_cast<uint32_t>(cnt[ui]);
+        const uint32_t Nu = static_cast<uint32_t>(cnt[vmax + ui]);
+        const uint32_t Ru = static_cast<uint32_t>(cnt[2 * vmax + ui]);
         const int nnu = __popc(dir_mask(u, s));
         if (GEN && pm) {  // X = N F: a Delta adds cD, a NICD adds cN + k_a F (R never hops)
           const uint32_t Fu = static_cast<uint32_t>(u == s.centre) - Ru;
@@ -442,7 +459,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
         }
         if (((Du | Nu | Ru) >= q.small) && fire_ok) {
           bool o2 = false;  // large counts: check the new total exactly
-          seg_voxel_total<GEN>(cnt, vmax, u, s, q, pm, o2);
+          seg_voxel_total<GEN>(cnt, vmax, u, s, q, pm, o2, oob);
           ovf |= o2;
         }
       }
@@ -461,10 +478,10 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
         for (int kq = 0; kq < (1 << qb); ++kq) {
           const int off = (sl << qb) + kq;  // position inside the block
           const int iv = (bv << s.lb) + off;
-          if (off >= (v & (s.B - 1)) && iv < s.V) pre[iv] += dv;
+          if (off >= (v & (s.B - 1)) && iv < s.V) pre[TSG_IDX(iv, vmax, oob)] += dv;
           if (u >= 0) {
             const int iu = ((u >> s.lb) << s.lb) + off;
-            if (off >= (u & (s.B - 1)) && iu < s.V) pre[iu] += du;
+            if (off >= (u & (s.B - 1)) && iu < s.V) pre[TSG_IDX(iu, vmax, oob)] += du;
           }
         }
       }
@@ -476,6 +493,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
       if (ovf) err |= kErrOverflow;
     }
     if (bad || bad_u) err |= kErrInternal;
+    if (kChecked && oob && act) err |= kErrBounds;
     __syncwarp();
 
     // ---- a segment whose cell is finished writes it back ------------------

@@ -30,6 +30,13 @@ __device__ __forceinline__ void wm_cell(const TissueView& t, const uint32_t cell
   const int centre = (n >> 1) * n + (n >> 1);
   const bool pm = t.q.kind == kModelPromoter;
   const QRates& q = t.q;
+  if (kChecked && (V > vmax || cell >= t.width * t.height)) {
+    // checked build: the cell does not fit the launch or is not in its tissue
+    if (sl == 0) atomicOr(t.err, kErrBounds);
+    __syncwarp(kFull);
+    return;
+  }
+  bool oob = false;  // checked build (see TSG_IDX)
   int32_t* g = t.counts + static_cast<size_t>(cell) * 3 * V;
   const uint32_t step = *t.step + step_off;
   const uint32_t key0 = static_cast<uint32_t>(t.seed), key1 = static_cast<uint32_t>(t.seed >> 32);
@@ -125,7 +132,7 @@ __device__ __forceinline__ void wm_cell(const TissueView& t, const uint32_t cell
     for (int sp = 0; sp < 3; ++sp) {
       const uint64_t T = sp == 0 ? D : sp == 1 ? N : R;
       if (pm && sp == 2) {
-        if (sl == 0) cnt[2 * vmax + centre] = static_cast<int32_t>(T);
+        if (sl == 0) cnt[2 * vmax + TSG_IDX(centre, vmax, oob)] = static_cast<int32_t>(T);
         continue;
       }
       const uint32_t w3 = t.tissue_id | ((kTagPlace + static_cast<uint32_t>(sp)) << 24);
@@ -135,7 +142,9 @@ __device__ __forceinline__ void wm_cell(const TissueView& t, const uint32_t cell
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           if (4 * blk + k < T)
-            atomicAdd(&cnt[sp * vmax + static_cast<int>(__umulhi(ws[k], static_cast<uint32_t>(V)))],
+            atomicAdd(&cnt[sp * vmax + TSG_IDX(static_cast<int>(__umulhi(
+                                                        ws[k], static_cast<uint32_t>(V))),
+                                                    vmax, oob)],
                       1);
       }
     }
@@ -143,6 +152,7 @@ __device__ __forceinline__ void wm_cell(const TissueView& t, const uint32_t cell
     for (int sp = 0; sp < 3; ++sp)
       for (int v = sl; v < V; v += H) g[sp * V + v] = cnt[sp * vmax + v];
   }
+  if (kChecked && __any_sync(kFull, oob)) err |= kErrBounds;
   if (sl == 0) {
     t.ev_last[cell] = e;
     t.t_last[cell] = tnow;

@@ -27,9 +27,11 @@ __device__ __forceinline__ void sig_face(const TissueView& t, const uint32_t c, 
                                          const double dt) {
   const int lane = threadIdx.x & 31;
   const uint32_t W = t.width, H = t.height;
-  const uint32_t nb = axis == 0 ? c + 1 : c + W;
+  bool oob = false;  // checked build: a cell outside the tissue (see TSG_IDX)
+  const uint32_t nb = static_cast<uint32_t>(TSG_IDX(axis == 0 ? c + 1 : c + W, W * H, oob));
+  const uint32_t ca = static_cast<uint32_t>(TSG_IDX(c, W * H, oob));
   const int n = static_cast<int>(t.n), V = static_cast<int>(t.V);
-  int32_t* ga = t.counts + static_cast<size_t>(c) * 3 * V;
+  int32_t* ga = t.counts + static_cast<size_t>(ca) * 3 * V;
   int32_t* gb = t.counts + static_cast<size_t>(nb) * 3 * V;
   const bool act = lane < n;
   const int va = axis == 0 ? lane * n + (n - 1) : (n - 1) * n + lane;
@@ -64,6 +66,7 @@ __device__ __forceinline__ void sig_face(const TissueView& t, const uint32_t c, 
   const uint32_t key0 = static_cast<uint32_t>(t.seed), key1 = static_cast<uint32_t>(t.seed >> 32);
   const uint32_t word3 = t.tissue_id | (tag << 24);
   int err = __any_sync(kFull, ovf) ? kErrOverflow : 0;
+  if (kChecked && oob) err = kErrBounds;  // then no event runs and nothing is written
   double tnow = 0.0;
   uint32_t e = 0, e0 = 0;
   uint64_t Em = 0, Rnd = 0;
@@ -122,7 +125,7 @@ __device__ __forceinline__ void sig_face(const TissueView& t, const uint32_t c, 
     if (e == 0xFFFFFFFFu) err |= kErrEventIndex;
   }
 
-  if (act) {
+  if (act && !(kChecked && oob)) {
     ga[va] = Da;
     ga[V + va] = Na;
     ga[2 * V + va] = Ra;
@@ -133,9 +136,9 @@ __device__ __forceinline__ void sig_face(const TissueView& t, const uint32_t c, 
   if (lane == 0) {
     const uint32_t cells = W * H;
     const size_t row = static_cast<size_t>(1 + axis) * cells;
-    t.ev_last[row + c] = e;
-    t.t_last[row + c] = tnow;
-    t.ev_total[row + c] += e;
+    t.ev_last[row + ca] = e;
+    t.t_last[row + ca] = tnow;
+    t.ev_total[row + ca] += e;
     if (err) atomicOr(t.err, err);
   }
 }

@@ -15,6 +15,26 @@ namespace tsg {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // ---------------------------------------------------------------------------
+// Checked build (compiled with -DTISSUE_CHECKED; the stand-in for a memory
+// sanitizer).  TSG_IDX(i, n, flag) is the array index i when 0 <= i < n;
+// otherwise it sets `flag` (reported as a bounds error through the device
+// error flag) and gives 0, so the access lands on element 0 instead of
+// outside the array.  In the normal build it is i itself: no instruction.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long checked_index(long long i, long long n, bool& flag) {
+  const bool ok = i >= 0 && i < n;
+  flag |= !ok;
+  return ok ? i : 0;
+}
+#ifdef TISSUE_CHECKED
+#define TSG_IDX(i, n, flag) ::tsg::checked_index((i), (n), (flag))
+constexpr bool kChecked = true;
+#else
+#define TSG_IDX(i, n, flag) (i)
+constexpr bool kChecked = false;
+#endif
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
 // 32x32->64 multiplications whose high words are xored into the other
 // counter words with the round key; the key advances by the golden-ratio and

@@ -18,6 +18,7 @@ constexpr int kErrOverflow = 1;
 constexpr int kErrEventIndex = 2;
 constexpr int kErrInternal = 4;  // a selection invariant failed (never expected)
 constexpr int kErrState = 8;     // promoter model: more bound sites than sites in a voxel
+constexpr int kErrBounds = 16;   // checked build: an array index was out of range
 constexpr uint32_t kModelND = 0u;        // Hill-repressed Notch-Delta lattice model
 constexpr uint32_t kModelPromoter = 1u;  // the paper's promoter model (Sec. III-A1)
 constexpr int kCountMax = (1 << 30) - 1;      // largest count a voxel may hold

@@ -196,6 +196,7 @@ int device_error(tissue* t) {
   if (cudaMemcpyAsync(&h, t->d_err, sizeof(int), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess)
     return TISSUE_E_CUDA;
   if (cudaStreamSynchronize(t->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  if (h & kErrBounds) return TISSUE_E_BOUNDS;
   if (h & kErrInternal) return TISSUE_E_CUDA;
   if (h & kErrState) return TISSUE_E_STATE;
   return h ? TISSUE_E_OVERFLOW : TISSUE_OK;
@@ -664,6 +665,7 @@ const char* tissue_strerror(int code) {
     case TISSUE_E_TIMEOUT: return "device wait timed out";
     case TISSUE_E_BUDGET: return "memory budget exceeded";
     case TISSUE_E_STATE: return "more bound promoter sites than sites";
+    case TISSUE_E_BOUNDS: return "an index out of range (checked build)";
     default: return "unknown error";
   }
 }

@@ -126,6 +126,7 @@ extern "C" int tissue_step_noalloc(const tissue_desc* d, const tissue_model* m,
   if (cudaMemcpyAsync(&flag, &s->err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
     return TISSUE_E_CUDA;
   if (cudaStreamSynchronize(stream) != cudaSuccess) return TISSUE_E_CUDA;
+  if (flag & kErrBounds) return TISSUE_E_BOUNDS;
   if (flag & kErrInternal) return TISSUE_E_CUDA;
   return flag ? TISSUE_E_OVERFLOW : TISSUE_OK;
 }

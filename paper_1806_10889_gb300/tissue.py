@@ -24,6 +24,7 @@ DEFAULT_CHI_WPB = 4
 
 OK, E_ARG, E_NOMEM, E_NOMODEL, E_OVERFLOW, E_CUDA, E_TIMEOUT, E_BUDGET = 0, -1, -2, -3, -4, -5, -6, -7
 E_STATE = -9
+E_BOUNDS = -10
 
 
 class TissueError(RuntimeError):
@@ -112,8 +113,14 @@ SIGNATURES = {
 }
 
 
+def checked() -> bool:
+    """True when TISSUE_CHECKED=1 selects the range-checked build."""
+    return os.environ.get("TISSUE_CHECKED", "0") == "1"
+
+
 def library_path() -> str:
-    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libtissue.so")
+    name = "libtissue_checked.so" if checked() else "libtissue.so"
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", name)
 
 
 def lib(build_if_missing: bool = True) -> C.CDLL:
@@ -124,8 +131,8 @@ def lib(build_if_missing: bool = True) -> C.CDLL:
             path = library_path()
             if build_if_missing:
                 from .build import build, is_stale
-                if is_stale():
-                    build()
+                if is_stale(checked()):
+                    build(checked=checked())
             if not os.path.exists(path):
                 raise RuntimeError(f"libtissue.so is missing ({path}); run the build first")
             L = C.CDLL(path)

@@ -29,9 +29,9 @@
 //
 // Template parameters: H lanes per cell; PRE the shared-memory layout; QB
 // whether a lane may cover several voxels of a block (B > H, i.e. V > H^2);
-// GEN whether the launch may hold promoter-model tissues (false: Notch-Delta
-// only, with the model test folded away).  The launcher picks QB and GEN from
-// the largest cell and the models of the listed tissues.
+// GEN the models the launch holds: 0 Notch-Delta only, 1 either (each cell
+// tests its tissue's model), 2 promoter only (the test folded away).  The
+// launcher picks QB and GEN from the largest cell and the listed tissues.
 #pragma once
 #include "tissue_dev.cuh"
 
@@ -136,7 +136,7 @@ __device__ __forceinline__ uint64_t chan_cum(const ChanLane& c, const QRates& q,
          (c.f17 ? q.k_in * X : 0ull);
 }
 
-template <int H, bool PRE, bool QB, bool GEN>
+template <int H, bool PRE, bool QB, int GEN>
 __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
                                                  const TissueView* __restrict__ views,
                                                  const uint2* __restrict__ items,
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
         s.qb = 0;
         while ((H << s.qb) < s.B) ++s.qb;
         s.centre = (s.n >> 1) * s.n + (s.n >> 1);
-        pm = GEN && sv->q.kind == kModelPromoter;
+        pm = GEN == 2 || (GEN == 1 && sv->q.kind == kModelPromoter);
         const bool skip = kChecked && (s.V > vmax || cell >= sv->width * sv->height);
         if (skip) {
           // the cell does not fit this launch's shared memory, or is not in
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
             if (v < s.V) {
               // promoter model: bound sites never exceed the voxel's sites
               if (pm && cnt[2 * vmax + v] > static_cast<int32_t>(v == s.centre)) bad_state = true;
-              S += seg_voxel_total<GEN>(cnt, vmax, v, s, sv->q, pm, ovf, oob);
+              S += seg_voxel_total<(GEN != 0)>(cnt, vmax, v, s, sv->q, pm, ovf, oob);
               if (PRE) pre[TSG_IDX(v, vmax, oob)] = S;
             }
           }
@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
 
     // ---- one event of every active segment (the whole warp in step) -------
     const bool act = have;
+    const bool PM = GEN == 2 ? true : pm;  // this segment's cell runs the promoter model
     const int qb = QB ? s.qb : 0;  // log2 of the voxels a lane covers in the selected block
     int j = static_cast<int>(e - e0);
     // Draws come in batches of H events per segment.  A segment that has used
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
       bool unused = false;
       const bool mine = act && sl < s.B && vb + sl < s.V;
       uint64_t cx =
-          mine ? seg_voxel_total<GEN>(cnt, vmax, vb + sl, s, q, pm, unused, oob) : 0ull;
+          mine ? seg_voxel_total<(GEN != 0)>(cnt, vmax, vb + sl, s, q, PM, unused, oob) : 0ull;
 #pragma unroll
       for (int o = 1; o < H; o <<= 1) {
         const uint64_t y = __shfl_up_sync(kFull, cx, o, H);
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     const uint32_t R = static_cast<uint32_t>(cnt[2 * vmax + vi]);
     const uint32_t hm = dir_mask(v, s);
     uint64_t c0, c1, X;
-    voxel_terms<GEN>(pm, q, v, s, D, N, R, act, c0, c1, X);
+    voxel_terms<(GEN != 0)>(PM, q, v, s, D, N, R, act, c0, c1, X);
     const uint64_t C = chan_cum(cl, q, c0, c1, D, N, R, X, hm);
     const uint64_t Cb = H == 8 ? chan_cum(cl2, q, c0, c1, D, N, R, X, hm) : ~0ull;
     uint64_t C16 = 0, C17 = 0, C18;
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
       // Notch-Delta: slot 17 is D + N -> R, 18 is R -> D + N.  Promoter:
       // slot 1 (unbinding) also frees the site (R - 1), slot 17 (binding) is
       // N + F -> R, and slots 4, 13..16 and 18 have no propensity.
-      const bool pm1 = GEN && pm && ch == 1, pm17 = GEN && pm && ch == 17;
+      const bool pm1 = GEN != 0 && PM && ch == 1, pm17 = GEN != 0 && PM && ch == 17;
       // the three lanes' (species, change, voxel), chosen without branches
       const int sp0 = ch <= 1 ? ch : ch <= 4 ? ch - 2 : hop ? hs : ch == 17 ? (pm17 ? 1 : 0) : 2;
       const int dd0 = ch <= 1 ? 1 : -1;
@@ -432,12 +433,13 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     uint64_t dv, du;
     if (PRE) {
       const uint64_t a_new =
-          act ? seg_voxel_total<GEN>(cnt, vmax, (sl == 1 && u >= 0) ? u : v, s, q, pm, ovf, oob)
+          act ? seg_voxel_total<(GEN != 0)>(cnt, vmax, (sl == 1 && u >= 0) ? u : v, s, q, PM, ovf,
+                                             oob)
               : 0ull;
       dv = __shfl_sync(kFull, a_new, 0, H) - a_old_v;
       du = __shfl_sync(kFull, a_new, 1, H) - a_old_u;
     } else {
-      dv = (act ? seg_voxel_total<GEN>(cnt, vmax, v, s, q, pm, ovf, oob) : 0ull) - a_old_v;
+      dv = (act ? seg_voxel_total<(GEN != 0)>(cnt, vmax, v, s, q, PM, ovf, oob) : 0ull) - a_old_v;
       // one molecule of species hs arrived at u: the change of u's total in
       // closed form (the total is affine in D and N apart from k_in X)
       du = 0;
@@ -447,7 +449,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
         const uint32_t Nu = static_cast<uint32_t>(cnt[vmax + ui]);
         const uint32_t Ru = static_cast<uint32_t>(cnt[2 * vmax + ui]);
         const int nnu = __popc(dir_mask(u, s));
-        if (GEN && pm) {  // X = N F: a Delta adds cD, a NICD adds cN + k_a F (R never hops)
+        if (GEN != 0 && PM) {  // X = N F: a Delta adds cD, a NICD adds cN + k_a F (R never hops)
           const uint32_t Fu = static_cast<uint32_t>(u == s.centre) - Ru;
           du = hs == 0 ? q.cD[nnu] : q.cN[nnu] + q.k_in * Fu;
         } else if (hs == 0) {
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
         }
         if (((Du | Nu | Ru) >= q.small) && fire_ok) {
           bool o2 = false;  // large counts: check the new total exactly
-          seg_voxel_total<GEN>(cnt, vmax, u, s, q, pm, o2, oob);
+          seg_voxel_total<(GEN != 0)>(cnt, vmax, u, s, q, PM, o2, oob);
           ovf |= o2;
         }
       }
@@ -485,7 +487,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
           }
         }
       }
-      if (GEN && sl == 0) trace_event(*sv, step, kTagChi, cell, e, tn, static_cast<uint32_t>(v),
+      if (GEN != 0 && sl == 0) trace_event(*sv, step, kTagChi, cell, e, tn, static_cast<uint32_t>(v),
                                       static_cast<uint32_t>(ch));
       tnow = tn;
       ++e;

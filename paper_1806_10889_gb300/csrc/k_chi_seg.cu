@@ -1,12 +1,13 @@
 // K_chi, persistent segmented form: the Notch-Delta-only instantiations and
-// the launcher (the kernel template is in chi_seg.cuh).
+// the launcher (the kernel template is in chi_seg.cuh; the model-generic and
+// promoter-only instantiations are in k_chi_seg_gen.cu and k_chi_seg_pm.cu).
 #include "chi_seg.cuh"
 
 namespace tsg {
 
 namespace {
 
-template <bool GEN>
+template <int GEN>
 ChiSegKernel pick(int H, bool pre, bool qb) {
   if (H == 8) {
     if (!pre) return k_chi_seg<8, false, false, GEN>;
@@ -22,7 +23,7 @@ ChiSegKernel pick(int H, bool pre, bool qb) {
 
 }  // namespace
 
-ChiSegKernel chi_seg_kernel_nd(int H, bool pre, bool qb) { return pick<false>(H, pre, qb); }
+ChiSegKernel chi_seg_kernel_nd(int H, bool pre, bool qb) { return pick<0>(H, pre, qb); }
 
 int seg_lanes_for(uint32_t V, int want) {
   if (want == 16 && V <= 256) return 16;
@@ -37,7 +38,7 @@ uint32_t seg_bytes_for(uint32_t V, int H, bool pre) {
 
 cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
                            uint32_t* d_counter, uint32_t vmax_cells, int H, int warps_per_block,
-                           int blocks, uint32_t step_off, double dt, bool pre, bool gen,
+                           int blocks, uint32_t step_off, double dt, bool pre, int gen,
                            cudaStream_t stream) {
   if (n_items == 0) return cudaSuccess;
   if (H != 8 && H != 16 && H != 32) return cudaErrorInvalidValue;
@@ -49,7 +50,10 @@ cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint
   const uint32_t seg_bytes = seg_bytes_for(vmax_cells, H, pre);
   const size_t smem = static_cast<size_t>(warps_per_block) * (32 / H) * seg_bytes;
   const int threads = 32 * warps_per_block;
-  const ChiSegKernel k = gen ? chi_seg_kernel_gen(H, pre, qb) : chi_seg_kernel_nd(H, pre, qb);
+  if (gen < 0 || gen > 2) return cudaErrorInvalidValue;
+  const ChiSegKernel k = gen == 2   ? chi_seg_kernel_pm(H, pre, qb)
+                         : gen == 1 ? chi_seg_kernel_gen(H, pre, qb)
+                                    : chi_seg_kernel_nd(H, pre, qb);
   cudaError_t e = cudaSuccess;
   if (smem > 48 * 1024)
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));

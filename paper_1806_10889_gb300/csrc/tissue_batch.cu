@@ -29,7 +29,7 @@ struct ClassPlan {
   uint32_t lanes, warps_per_block, layout;
   size_t items_off;  // offset (in uint2) into the item buffer
   uint32_t n_items;
-  bool gen;          // some member of the class runs the promoter model
+  int gen;           // 0: Notch-Delta only; 2: promoter only; 1: both, or a trace is on
 };
 
 }  // namespace
@@ -122,13 +122,14 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
 
   // chi items by class, largest cells first; faces of both phases
   std::map<uint32_t, std::vector<uint2>, std::greater<uint32_t>> by_v;
-  std::map<uint32_t, bool> gen_v;
+  std::map<uint32_t, int> nd_v, pm_v, tr_v;  // per class: members of each model, traced
   std::vector<uint2> xf, yf, wm_items;
   for (uint32_t i = 0; i < count; ++i) {
     const tissue_desc& d = info[i].desc;
     const uint32_t V = d.n * d.n, cells = d.width * d.height;
     std::vector<uint2>& list = by_v[V];
-    gen_v[V] = gen_v[V] || info[i].view.q.kind != kModelND || info[i].view.trace != nullptr;
+    (info[i].view.q.kind == kModelPromoter ? pm_v : nd_v)[V] += 1;
+    if (info[i].view.trace != nullptr) tr_v[V] += 1;
     const uint8_t* wm = info[i].wm_host;
     for (uint32_t c = 0; c < cells; ++c) {
       if (wm && wm[c]) {
@@ -155,7 +156,8 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
     p.layout = dl.smem_layout;
     p.items_off = items.size();
     p.n_items = static_cast<uint32_t>(kv.second.size());
-    p.gen = gen_v[kv.first];
+    const uint32_t V = kv.first;
+    p.gen = (nd_v[V] == 0 && pm_v[V] > 0) ? 2 : (pm_v[V] > 0 || tr_v[V] > 0) ? 1 : 0;
     items.insert(items.end(), kv.second.begin(), kv.second.end());
     b->classes.push_back(p);
   }

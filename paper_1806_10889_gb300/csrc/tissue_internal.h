@@ -102,16 +102,18 @@ cudaError_t launch_chi(const TissueView& t, uint32_t step_off, double dt, int wa
 // picks a grid that fills every SM.
 // pre: keep the per-voxel prefix array (layout 0) or recompute the selected
 // block (layout 1, at most 4 warps per block).
-// gen: the launch may hold promoter-model tissues (instantiations that test
-// each tissue's model); false runs the Notch-Delta-only code.
+// gen: the models of the listed tissues: 0 Notch-Delta only (the fast
+// path), 1 either or a trace is on (each cell tests its tissue's model), 2
+// promoter only.
 cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
                            uint32_t* d_counter, uint32_t vmax_cells, int H, int warps_per_block,
-                           int blocks, uint32_t step_off, double dt, bool pre, bool gen,
+                           int blocks, uint32_t step_off, double dt, bool pre, int gen,
                            cudaStream_t stream);
 using ChiSegKernel = void (*)(const TissueView*, const uint2*, uint32_t, uint32_t*, uint32_t,
                               uint32_t, double);
 ChiSegKernel chi_seg_kernel_nd(int H, bool pre, bool qb);   // k_chi_seg.cu
 ChiSegKernel chi_seg_kernel_gen(int H, bool pre, bool qb);  // k_chi_seg_gen.cu
+ChiSegKernel chi_seg_kernel_pm(int H, bool pre, bool qb);   // k_chi_seg_pm.cu
 uint32_t seg_bytes_for(uint32_t V, int H, bool pre);
 // Well-mixed cells (k_chi_wm.cu): one warp per (tissue, cell) item;
 // vmax_cells is the largest V among the listed cells.

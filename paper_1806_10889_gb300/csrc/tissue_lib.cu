@@ -162,7 +162,8 @@ cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt
                           t->d_work, v.V, static_cast<int>(c.lanes_per_cell),
                           static_cast<int>(c.warps_per_block), static_cast<int>(c.blocks), i, dt,
                           c.smem_layout == TISSUE_LAYOUT_PREFIX,
-                          t->q.kind != kModelND || t->d_trace != nullptr, t->stream);
+                          t->q.kind == kModelPromoter ? 2 : t->d_trace != nullptr ? 1 : 0,
+                          t->stream);
   }
   return launch_chi(v, i, dt, static_cast<int>(c.warps_per_block), t->stream);
 }

@@ -512,6 +512,101 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _gpu_rate(spec, dt, steps, burn=0, config=None):
+    """Device-timed rate of `steps` splitting steps after `burn` untimed ones:
+    (events/s, cell-steps/s, events per step, device ms per step)."""
+    import torch
+
+    from paper_1806_10889_gb300.tissue import Tissue
+
+    g = Tissue(spec)
+    if config:
+        g.set_launch_config(*config)
+    if burn:
+        g.step(dt, burn)
+    g.step(dt, 1)
+    g.sync()
+    stream = torch.cuda.current_stream()
+    ev0 = g.total_events()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    g.step(dt, steps)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    ev = float((g.total_events() - ev0).sum())
+    g.close()
+    return ev / (ms / 1e3), spec.cells * steps / (ms / 1e3), ev / steps, ms / steps
+
+
+def _cpu_rate(spec, dt, steps, burn_state=None, step0=0, cells=None, threads=0):
+    """The oracle's rate: whole-tissue steps (all cores) or, with `cells`,
+    chi of those cells only (one core is enough for a subset)."""
+    import oracle as O
+    d = O.Desc(spec.width, spec.height, spec.n, seed=spec.seed, tissue_id=spec.tissue_id,
+               init_lambda=tuple(spec.init_lambda))
+    m = O.Model(**spec.model)
+    if burn_state is not None:
+        counts = np.array(burn_state, copy=True)
+    elif cells is None:
+        counts = O.init_counts(d)
+    else:  # only the cells timed need initial counts
+        counts = np.zeros(spec.cells * 3 * spec.V, dtype=np.int32)
+        for c in cells:
+            O.init_cell(d, counts, int(c))
+    threads = threads or O.max_threads()
+    t0, ev = time.perf_counter(), 0
+    if cells is None:
+        for k in range(steps):
+            ne, _ = O.step(d, m, counts, step0 + k, 1, dt, n_threads=threads)
+            ev += int(ne.sum())
+        return ev / (time.perf_counter() - t0), threads
+    for c in cells:
+        ev += O.chi_cell(d, m, counts, int(c), step0, dt)[0]
+    return ev / (time.perf_counter() - t0), 1
+
+
+def run_suite(args) -> dict:
+    """Every configuration of the benchmark suite on this GPU, with the
+    oracle beside it (host cores, all and one), for the results table."""
+    from paper_1806_10889_gb300.tissue import Tissue
+
+    out = {}
+    peaks, _ = _peaks()
+    hbm = peaks["hbm_gbs"] * 1e9
+
+    def row(name, spec, dt, steps, burn, cpu_steps=2, cpu_cells=256):
+        ev_s, cs_s, ev_step, ms = _gpu_rate(spec, dt, steps, burn)
+        state = None
+        if burn:  # the oracle starts from the same burned-in state
+            g = Tissue(spec)
+            g.step(dt, burn)
+            state, step0 = g.read_counts(), g.get_step()
+            g.close()
+        else:
+            step0 = 0
+        all_cores, thr = _cpu_rate(spec, dt, cpu_steps, state, step0) if cpu_steps else (None, 0)
+        one_core, _ = _cpu_rate(spec, dt, 1, state, step0,
+                                cells=range(min(cpu_cells, spec.cells)))
+        out[name] = {"gpu_events_per_s": ev_s, "gpu_cell_steps_per_s": cs_s,
+                     "events_per_step": ev_step, "gpu_ms_per_step": ms,
+                     "hbm_frac": 24 * spec.V * cs_s / hbm,
+                     "cpu_events_per_s": all_cores, "cpu_cores": thr,
+                     "cpu_1core_events_per_s": one_core,
+                     "cpu_sample": f"{cpu_steps} whole-tissue steps (all cores); chi of "
+                                   f"{min(cpu_cells, spec.cells)} cells (one core)",
+                     "dt": dt, "burn_in_steps": burn, "timed_steps": steps}
+
+    tiny = W.tiny()
+    row("tiny", tiny.tissue, tiny.dt, tiny.n_steps, 0, cpu_steps=tiny.n_steps)
+    for dt, burn, steps in ((0.01, 2000, 50), (0.1, 200, 10), (1.0, 20, 3)):
+        row(f"medium_dt{dt}", W.medium(dt).tissue, dt, steps, burn, cpu_steps=2 if dt < 1 else 1)
+    lg = W.large()
+    row("large", lg.tissue, lg.dt, 2, 0, cpu_steps=0, cpu_cells=128)
+    out["large"]["cpu_sample"] = "chi of 128 cells at step 0 (one core); all cores not run"
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -543,10 +638,16 @@ def main():
                     help="serve the first K requests of the serving workload (0: skip)")
     ap.add_argument("--serving-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--suite", action="store_true",
+                    help="measure every configuration of the suite (GPU and oracle) and print "
+                         "one JSON object instead of the benchmark line (several minutes)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     rank, world, local_rank = _env_rank()
+    if args.suite:
+        print(json.dumps(run_suite(args)))
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:

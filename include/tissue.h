@@ -220,9 +220,11 @@ typedef struct {
   uint32_t blocks;          /* persistent kernel grid; 0 = enough to fill every SM */
   uint32_t smem_layout;     /* persistent kernel: TISSUE_LAYOUT_PREFIX or _RECOMPUTE */
 } tissue_launch;
-/* The default after tissue_create, by cell size: persistent kernel, prefix
- * layout, with 8 lanes and 4 warps per block for V <= 64, 16 lanes and 4
- * warps for V <= 256, 32 lanes and 2 warps above. */
+/* The default after tissue_create: persistent kernel, prefix layout; for a
+ * tissue of at most 1024 cells 32 lanes and 2 warps per block (one cell per
+ * warp: the shortest event chain, which sets the time when the machine is
+ * not full); otherwise by cell size, 8 lanes and 4 warps per block for
+ * V <= 64, 16 lanes and 4 warps for V <= 256, 32 lanes and 2 warps above. */
 int tissue_set_launch_config(tissue* t, const tissue_launch* config);
 int tissue_get_launch_config(const tissue* t, tissue_launch* config);
 

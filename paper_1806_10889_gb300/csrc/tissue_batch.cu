@@ -150,7 +150,7 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
     if (kv.second.empty()) continue;  // every cell of this size is well-mixed
     ClassPlan p{};
     p.V = kv.first;
-    const tissue_launch dl = default_launch(kv.first);
+    const tissue_launch dl = default_launch(kv.first, kv.second.size());
     p.lanes = dl.lanes_per_cell;
     p.warps_per_block = dl.warps_per_block;
     p.layout = dl.smem_layout;

@@ -132,8 +132,9 @@ struct TissueInfo {
   const uint8_t* wm_host;  // per cell: 1 = well-mixed (host copy); nullptr if none
 };
 bool tissue_info(const tissue* t, TissueInfo* out);
-// The default chi launch for cells of V voxels.
-tissue_launch default_launch(uint32_t V);
+// The default chi launch for `cells` cells of V voxels (one launch).
+constexpr uint64_t kFewCells = 1024;
+tissue_launch default_launch(uint32_t V, uint64_t cells);
 void tissue_advance_host_step(tissue* t, uint32_t n);
 int seg_lanes_for(uint32_t V, int want);
 

@@ -138,7 +138,14 @@ cudaError_t tsg::lib_malloc(void** p, size_t bytes) {
   return cudaMalloc(p, bytes);
 }
 
-tissue_launch tsg::default_launch(uint32_t V) {
+tissue_launch tsg::default_launch(uint32_t V, uint64_t cells) {
+  // Up to ~1,000 cells the machine is not full and each cell's event chain
+  // sets the time: one cell per warp has the shortest chain (measured:
+  // 2,790 against 2,930 and 3,220 SM cycles per event with 16 and 8 lanes on
+  // four 8x8 cells).  Beyond that, cells sharing a warp share its
+  // instruction issue.
+  if (cells <= kFewCells) return tissue_launch{TISSUE_KERNEL_PERSISTENT, 32, 2, 0,
+                                               TISSUE_LAYOUT_PREFIX};
   if (V <= 64) return tissue_launch{TISSUE_KERNEL_PERSISTENT, 8, 4, 0, TISSUE_LAYOUT_PREFIX};
   if (V <= 256) return tissue_launch{TISSUE_KERNEL_PERSISTENT, 16, 4, 0, TISSUE_LAYOUT_PREFIX};
   return tissue_launch{TISSUE_KERNEL_PERSISTENT, 32, 2, 0, TISSUE_LAYOUT_PREFIX};
@@ -318,7 +325,7 @@ int tissue_create(const tissue_desc* d, void* dev_counts, size_t bytes, void* cu
   // Default chi launch (measured on GB300): the persistent kernel with four
   // cells per warp for V <= 64, two for V <= 256, one (2 warps per block)
   // above.
-  t->cfg = default_launch(d->n * d->n);
+  t->cfg = default_launch(d->n * d->n, cells_of(d));
   const ScratchLayout L = layout(d);
   if (lib_malloc(reinterpret_cast<void**>(&t->scratch), L.total) != cudaSuccess) {
     cudaGetLastError();

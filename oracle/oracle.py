@@ -205,6 +205,10 @@ def lib():
                                           C.c_uint32, C.c_double, C.c_void_p, C.c_size_t,
                                           P(C.c_size_t)]
             L.orc_step_traced.restype = C.c_int
+            L.orc_step_traced_scheme.argtypes = [P(_Desc), P(_Model), C.c_void_p, C.c_uint32,
+                                                 C.c_uint32, C.c_double, C.c_int, C.c_void_p,
+                                                 C.c_size_t, P(C.c_size_t)]
+            L.orc_step_traced_scheme.restype = C.c_int
             L.orc_set_mutation.argtypes = [C.c_int]
             L.orc_set_mutation.restype = None
             L.orc_set_paranoid.argtypes = [C.c_int]
@@ -328,14 +332,14 @@ def step(d: Desc, m: Model, counts: np.ndarray, step0: int, n_steps: int, dt: fl
 
 
 def step_traced(d: Desc, m: Model, counts: np.ndarray, step0: int, n_steps: int, dt: float,
-                trace_cap: int = 1 << 22):
+                trace_cap: int = 1 << 22, scheme: int = 0):
     """Like step() but single-threaded, returning every fired event in order."""
     _check_state(d, counts)
     dc, mc = d.to_c(), m.to_c()
     tr = np.zeros(trace_cap, dtype=EVENT_DTYPE)
     tlen = C.c_size_t()
-    rc = lib().orc_step_traced(C.byref(dc), C.byref(mc), _ptr(counts), step0, n_steps, dt,
-                               _ptr(tr), trace_cap, C.byref(tlen))
+    rc = lib().orc_step_traced_scheme(C.byref(dc), C.byref(mc), _ptr(counts), step0, n_steps,
+                                      dt, int(scheme), _ptr(tr), trace_cap, C.byref(tlen))
     if rc:
         raise OracleError(rc, "step_traced")
     if tlen.value > trace_cap:

@@ -788,7 +788,14 @@ int orc_step_scheme(const orc_desc* d, const orc_model* m, int32_t* counts, uint
 int orc_step_traced(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_t step0,
                     uint32_t n_steps, double dt, orc_event* trace, size_t trace_cap,
                     size_t* trace_len) {
+  return orc_step_traced_scheme(d, m, counts, step0, n_steps, dt, 0, trace, trace_cap,
+                                trace_len);
+}
+
+int orc_step_traced_scheme(const orc_desc* d, const orc_model* m, int32_t* counts,
+                           uint32_t step0, uint32_t n_steps, double dt, int scheme,
+                           orc_event* trace, size_t trace_cap, size_t* trace_len) {
   *trace_len = 0;
-  return step_impl(d, m, counts, step0, n_steps, dt, 0, NULL, NULL, 1, trace, trace_cap,
+  return step_impl(d, m, counts, step0, n_steps, dt, scheme, NULL, NULL, 1, trace, trace_cap,
                    trace_len);
 }

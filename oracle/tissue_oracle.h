@@ -155,6 +155,10 @@ int orc_step_scheme(const orc_desc* d, const orc_model* m, int32_t* counts, uint
 int orc_step_traced(const orc_desc* d, const orc_model* m, int32_t* counts, uint32_t step0,
                     uint32_t n_steps, double dt, orc_event* trace, size_t trace_cap,
                     size_t* trace_len);
+/* As orc_step_traced, with the splitting scheme of orc_step_scheme. */
+int orc_step_traced_scheme(const orc_desc* d, const orc_model* m, int32_t* counts,
+                           uint32_t step0, uint32_t n_steps, double dt, int scheme,
+                           orc_event* trace, size_t trace_cap, size_t* trace_len);
 
 /* Test hooks: 0 = faithful.  A nonzero value plants one known mistake so the
  * pin tests can show that they catch it. */

@@ -25,18 +25,20 @@ from paper_1806_10889_gb300.tissue import Tissue  # noqa: E402
 P, PRE, REC = T.KERNEL_PERSISTENT, T.LAYOUT_PREFIX, T.LAYOUT_RECOMPUTE
 
 
-def _oracle_trace(spec, dt, n_steps):
+def _oracle_trace(spec, dt, n_steps, scheme=O.LIE):
     d, m = orc_desc(spec), orc_model(spec)
     counts = O.init_counts(d)
-    tr = O.step_traced(d, m, counts, 0, n_steps, dt, trace_cap=1 << 23)
+    tr = O.step_traced(d, m, counts, 0, n_steps, dt, trace_cap=1 << 23, scheme=scheme)
     tr = np.sort(tr, order=["step", "kind", "unit", "e"])
     return counts, tr
 
 
-def _gpu_trace(spec, dt, n_steps, config=None, cap=1 << 23):
+def _gpu_trace(spec, dt, n_steps, config=None, cap=1 << 23, scheme=O.LIE):
     g = Tissue(spec)
     if config:
         g.set_launch_config(*config)
+    if scheme == O.STRANG:
+        g.set_splitting(T.SPLIT_STRANG)
     g.trace_begin(cap)
     g.step(dt, n_steps)
     counts = g.read_counts()
@@ -110,3 +112,14 @@ def test_trace_overflow_and_warp_kernel_are_reported():
     g.step(0.1, 1)  # the warp kernel runs again without a trace
     g.sync()
     g.close()
+
+
+def test_event_log_strang_splitting():
+    """Strang's five module calls per step, the second face halves on their
+    own Philox tags (5 and 6)."""
+    spec = TissueSpec(3, 3, 8, seed=39).with_model(k_bind=0.05)
+    c_ref, t_ref = _oracle_trace(spec, 0.1, 4, O.STRANG)
+    c_gpu, t_gpu = _gpu_trace(spec, 0.1, 4, scheme=O.STRANG)
+    assert np.array_equal(c_gpu, c_ref)
+    assert set(np.unique(t_ref["kind"])) == {1, 2, 3, 5, 6}
+    _same(t_gpu, t_ref)

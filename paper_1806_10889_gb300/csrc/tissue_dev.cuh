@@ -159,44 +159,41 @@ struct F53 {
   int k;       // x ~ m * 2^(k - 52)
 };
 
-// Round x >= 1 to 53 significant bits, half to even (the u64 -> binary64 rule).
+// Round x >= 1 to 53 significant bits, half to even: by definition the
+// u64 -> binary64 conversion, so the hardware conversion does it in one
+// instruction; the significand (with its leading bit) and the exponent are
+// then read from the bits.
 __device__ __forceinline__ F53 round53(uint64_t x) {
-  const int k = 63 - __clzll(static_cast<long long>(x));
-  if (k <= 52) return F53{x << (52 - k), k};
-  const int s = k - 52;
-  uint64_t m = x >> s;
-  const uint64_t rem = x & ((1ull << s) - 1ull), half = 1ull << (s - 1);
-  m += static_cast<uint64_t>((rem > half) | ((rem == half) & static_cast<bool>(m & 1ull)));
-  if (m >> 53) return F53{m >> 1, k + 1};
-  return F53{m, k};
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(__ull2double_rn(x)));
+  return F53{(b & ((1ull << 52) - 1ull)) | (1ull << 52), static_cast<int>(b >> 52) - 1023};
 }
 
-// floor(2^115 / d) within +-2, d in (2^52, 2^53).  Seed y0 = m24 * 2^s0 from
+// floor(2^115 / d) within +-2, d in (2^52, 2^53).  Seed y0 = m24 * 2^39 from
 // the single-precision reciprocal of d's top 24 bits (relative error < 2^-21),
 // then one third-order step y = y0 (1 + e + e^2), e = 1 - d y0 / 2^115, which
-// leaves a relative error near e^3 < 2^-63.  d*y0 differs from 2^115 by less
-// than 2^(s0+54), so e is exact from the low 64 bits of d*m24.
+// leaves a relative error near e^3 < 2^-63.  The reciprocal of d >> 29, a
+// value in [2^23, 2^24), lies in (2^-24, 2^-23]; capping it just below 2^-23
+// keeps its exponent, and so every shift below, constant.  d*y0 differs from
+// 2^115 by less than 2^94 (|e'| < 2^55 below), so e is exact from the low 64
+// bits of d*m24.
 __device__ __forceinline__ uint64_t recip115(uint64_t d) {
   const float df = static_cast<float>(static_cast<uint32_t>(d >> 29));  // exact: < 2^24
   float f;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"(df));
-  const uint32_t fb = __float_as_uint(f);
-  const int s0 = static_cast<int>((fb >> 23) & 0xFFu) - 127 + 63;  // 39 or 40
-  const uint32_t m24 = (fb & 0x7FFFFFu) | 0x800000u;
-  // e * 2^(115 - s0) = 2^(115 - s0) - d*m24; the power of two vanishes mod 2^64
+  f = fminf(f, __uint_as_float(0x33FFFFFFu));  // largest float below 2^-23
+  const uint32_t m24 = (__float_as_uint(f) & 0x7FFFFFu) | 0x800000u;  // y0 = m24 * 2^39
+  // e * 2^76 = 2^76 - d*m24; the power of two vanishes mod 2^64
   const int64_t e = -static_cast<int64_t>(d * static_cast<uint64_t>(m24));
   const uint64_t ae = static_cast<uint64_t>(e < 0 ? -e : e);
-  // t1 = y0 |e| = m24 |e'| / 2^(115 - 2 s0), from the 32-bit halves of |e'|
-  const int sh = 115 - 2 * s0;  // 37 or 35
+  // t1 = y0 |e| = m24 |e'| / 2^37, from the 32-bit halves of |e'|
   const uint64_t P1 = static_cast<uint64_t>(m24) * static_cast<uint32_t>(ae >> 32);
   const uint64_t P0 = static_cast<uint64_t>(m24) * static_cast<uint32_t>(ae);
-  const uint64_t t1 =
-      (P1 >> (sh - 32)) + ((((P1 & ((1ull << (sh - 32)) - 1ull)) << 32) + P0) >> sh);
-  // t2 = y0 e^2 = m24 e'^2 / 2^(230 - 3 s0) >= 0, to a fraction of a unit
-  const uint64_t e24 = ae >> 24;            // < 2^30
+  const uint64_t t1 = (P1 >> 5) + ((((P1 & 31ull) << 32) + P0) >> 37);
+  // t2 = y0 e^2 = m24 e'^2 / 2^113 >= 0, to a fraction of a unit
+  const uint64_t e24 = ae >> 24;            // < 2^31
   const uint64_t e2 = (e24 * e24) >> 24;    // e'^2 / 2^72
-  const uint64_t t2 = (static_cast<uint64_t>(m24) * e2) >> (158 - 3 * s0);
-  const uint64_t y0 = static_cast<uint64_t>(m24) << s0;
+  const uint64_t t2 = (static_cast<uint64_t>(m24) * e2) >> 41;
+  const uint64_t y0 = static_cast<uint64_t>(m24) << 39;
   return (e >= 0 ? y0 + t1 : y0 - t1) + t2;
 }
 

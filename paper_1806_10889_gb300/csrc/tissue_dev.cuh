@@ -204,22 +204,22 @@ __device__ __forceinline__ double tau_from(const F53 eq, bool e_zero, uint64_t A
   const F53 a = round53(A);
   const uint64_t mE = eq.m, d = a.m;
   const int sh = mE >= d ? 52 : 53;  // quotient significand lands in [2^52, 2^53)
-  uint64_t q;
-  int64_t r;
+  // h = floor(mE 2^(sh+1) / d): the quotient with one more bit.  The quotient
+  // of two 53-bit significands is never exactly half-way between two 53-bit
+  // values, so the rounded quotient is (h + 1) >> 1.
+  uint64_t h;
   if (d == (1ull << 52)) {           // power-of-two divisor: exact shift
-    q = mE << (sh - 52);
-    r = 0;
+    h = mE << (sh - 51);
   } else {
     const uint64_t y = recip115(d);
     const uint64_t plo = mE * y, phi = __umul64hi(mE, y);
-    q = sh == 52 ? ((phi << 1) | (plo >> 63)) : ((phi << 2) | (plo >> 62));
+    h = sh == 52 ? ((phi << 2) | (plo >> 62)) : ((phi << 3) | (plo >> 61));
     // |y - 2^115/d| <= 2 makes the estimate off by at most one either way
-    r = static_cast<int64_t>((mE << sh) - q * d);  // exact: |r| < 2^55
-    if (r < 0) { q -= 1; r += static_cast<int64_t>(d); }
-    if (r >= static_cast<int64_t>(d)) { q += 1; r -= static_cast<int64_t>(d); }
+    int64_t r = static_cast<int64_t>((mE << (sh + 1)) - h * d);  // exact: |r| < 2^56
+    if (r < 0) { h -= 1; r += static_cast<int64_t>(d); }
+    if (r >= static_cast<int64_t>(d)) h += 1;
   }
-  const uint64_t twice = static_cast<uint64_t>(r) << 1;
-  q += static_cast<uint64_t>((twice > d) | ((twice == d) & static_cast<bool>(q & 1ull)));
+  const uint64_t q = (h + 1ull) >> 1;
   // tau = q * 2^X with X = (kE - 110) - (kA - 84) - sh; a carry of q into
   // 2^53 moves into the exponent field by itself.
   const int X = eq.k - a.k - 26 - sh;

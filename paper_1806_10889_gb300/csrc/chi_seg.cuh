@@ -125,15 +125,32 @@ __device__ __forceinline__ ChanLane chan_lane(int j) {
 // pre[] of the voxel propensities (20 B per voxel); false keeps only the
 // counts (12 B per voxel) and recomputes the selected block's propensities,
 // trading ~70 instructions per pass for ~40% more cells resident per SM.
-// Running sum C_j of the channels 0..j of a voxel (~0 for j >= 19).
-__device__ __forceinline__ uint64_t chan_cum(const ChanLane& c, const QRates& q, uint64_t c0,
-                                             uint64_t c1, uint32_t D, uint32_t N, uint32_t R,
-                                             uint64_t X, uint32_t hm) {
+// A lane's channel-sum coefficients for one tissue, in registers (set when the
+// segment takes a cell): the per-count terms of the channels up to the lane's.
+// The hop terms depend on the voxel's neighbours and are added per voxel.
+struct LaneK {
+  uint64_t aD, aN, aR, k17;  // gD, gN, gR + k_off and k_in where counted in C_j
+};
+
+__device__ __forceinline__ LaneK lane_k(const ChanLane& c, const QRates& q) {
+  LaneK k;
+  k.aD = c.f2 ? q.gD : 0ull;
+  k.aN = c.f3 ? q.gN : 0ull;
+  k.aR = (c.f4 ? q.gR : 0ull) + (c.f18 ? q.k_off : 0ull);
+  k.k17 = c.f17 ? q.k_in : 0ull;
+  return k;
+}
+
+// Running sum C_j of the channels 0..j of a voxel (~0 for j >= 19). The hop
+// rates, the same for every lane, come from the view in shared memory: holding
+// them in registers too costs a resident block per SM.
+__device__ __forceinline__ uint64_t chan_cum(const ChanLane& c, const LaneK& k, const QRates& q,
+                                             uint64_t c0, uint64_t c1, uint32_t D, uint32_t N,
+                                             uint32_t R, uint64_t X, uint32_t hm) {
   if (!c.valid) return ~0ull;
-  return c0 + (c.f1 ? c1 : 0ull) + D * ((c.f2 ? q.gD : 0ull) + q.hopD * __popc(hm & c.mD)) +
-         N * ((c.f3 ? q.gN : 0ull) + q.hopN * __popc(hm & c.mN)) +
-         R * ((c.f4 ? q.gR : 0ull) + q.hopR * __popc(hm & c.mR) + (c.f18 ? q.k_off : 0ull)) +
-         (c.f17 ? q.k_in * X : 0ull);
+  return c0 + (c.f1 ? c1 : 0ull) + D * (k.aD + q.hopD * __popc(hm & c.mD)) +
+         N * (k.aN + q.hopN * __popc(hm & c.mN)) + R * (k.aR + q.hopR * __popc(hm & c.mR)) +
+         k.k17 * X;
 }
 
 template <int H, bool PRE, bool QB, int GEN>
@@ -157,6 +174,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
   int32_t* cnt = reinterpret_cast<int32_t*>(base + kViewBytes + (PRE ? 8 * vmax : 0));
   const ChanLane cl = chan_lane(sl);
   const ChanLane cl2 = chan_lane(sl + H);  // second channel of each lane when H = 8
+  LaneK lk{}, lk2{};                         // their coefficients for the current cell
 
   static_assert(PRE || !QB, "the recompute layout needs B <= H");
   bool have = false, done = false, pm = false;
@@ -194,6 +212,8 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
         while ((H << s.qb) < s.B) ++s.qb;
         s.centre = (s.n >> 1) * s.n + (s.n >> 1);
         pm = GEN == 2 || (GEN == 1 && sv->q.kind == kModelPromoter);
+        lk = lane_k(cl, sv->q);
+        if (H == 8) lk2 = lane_k(cl2, sv->q);
         const bool skip = kChecked && (s.V > vmax || cell >= sv->width * sv->height);
         if (skip) {
           // the cell does not fit this launch's shared memory, or is not in
@@ -372,8 +392,8 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     const uint32_t hm = dir_mask(v, s);
     uint64_t c0, c1, X;
     voxel_terms<(GEN != 0)>(PM, q, v, s, D, N, R, act, c0, c1, X);
-    const uint64_t C = chan_cum(cl, q, c0, c1, D, N, R, X, hm);
-    const uint64_t Cb = H == 8 ? chan_cum(cl2, q, c0, c1, D, N, R, X, hm) : ~0ull;
+    const uint64_t C = chan_cum(cl, lk, q, c0, c1, D, N, R, X, hm);
+    const uint64_t Cb = H == 8 ? chan_cum(cl2, lk2, q, c0, c1, D, N, R, X, hm) : ~0ull;
     uint64_t C16 = 0, C17 = 0, C18;
     if (H <= 16) {
       // C_16..C_18 from C_15: +x hop of R (if that neighbour exists), slots 17, 18

@@ -53,7 +53,7 @@ ISSUE_PEAK_GINST = 152 * 4 * 2.070
 # timed chi launches / their chi events; profiles/k_chi_medium_metrics.md).
 CHI_INST_PER_EVENT = {("persistent", 16, 0): 298.0}
 # DRAM bytes (read + write) per chi launch from the same capture, per variant.
-CHI_TRAFFIC = {("persistent", 16, 0): None}
+CHI_TRAFFIC = {("persistent", 16, 0): 1.314e7}
 # Algorithmic DRAM bytes of one chi launch per cell: the state read + write.
 STATE_BYTES_PER_CELL_RW = lambda V: 2 * 3 * V * 4  # noqa: E731
 

@@ -211,7 +211,7 @@ int tissue_set_launch(tissue* t, uint32_t chi_warps_per_block);
  * computes the same trajectory bit for bit. */
 #define TISSUE_KERNEL_WARP 0u       /* one warp per cell, one launch over all cells */
 #define TISSUE_KERNEL_PERSISTENT 1u /* persistent kernel, cells taken from a work list */
-#define TISSUE_LAYOUT_PREFIX 0u    /* persistent kernel keeps per-voxel prefix sums (20 B/voxel) */
+#define TISSUE_LAYOUT_PREFIX 0u    /* persistent kernel keeps per-voxel prefix sums (20 B/voxel; 14 B with 16-bit counts, cells of V > 256) */
 #define TISSUE_LAYOUT_RECOMPUTE 1u /* counts only (12 B/voxel); <= 4 warps per block, V <= lanes^2 */
 typedef struct {
   uint32_t kernel;          /* TISSUE_KERNEL_WARP or TISSUE_KERNEL_PERSISTENT */

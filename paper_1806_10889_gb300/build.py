@@ -20,7 +20,7 @@ LIB = os.path.join(OUT, "libtissue.so")
 # checked and an out-of-range one is reported (TISSUE_E_BOUNDS) instead of
 # accessed.  The binding loads it when TISSUE_CHECKED=1.
 LIB_CHECKED = os.path.join(OUT, "libtissue_checked.so")
-SOURCES = ["k_chi.cu", "k_chi_seg.cu", "k_chi_seg_gen.cu", "k_chi_seg_pm.cu", "k_chi_wm.cu", "k_sig.cu", "tissue_lib.cu", "tissue_batch.cu", "tissue_noalloc.cu"]
+SOURCES = ["k_chi.cu", "k_chi_seg.cu", "k_chi_seg_gen.cu", "k_chi_seg_pm.cu", "k_chi_seg_narrow.cu", "k_chi_wm.cu", "k_sig.cu", "tissue_lib.cu", "tissue_batch.cu", "tissue_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "--expt-relaxed-constexpr",
                      "-Xcompiler", "-fPIC,-ffp-contract=off", f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -30,9 +30,16 @@
 // Template parameters: H lanes per cell; PRE the shared-memory layout; QB
 // whether a lane may cover several voxels of a block (B > H, i.e. V > H^2);
 // GEN the models the launch holds: 0 Notch-Delta only, 1 either (each cell
-// tests its tissue's model), 2 promoter only (the test folded away).  The
+// tests its tissue's model), 2 promoter only (the test folded away); NARROW
+// 16-bit counts in shared memory (14 instead of 20 bytes per voxel, so more
+// large cells fit on an SM).  A NARROW segment whose cell holds or reaches a
+// count above 65535 leaves that cell untouched and appends it to a redo list,
+// which the launcher then runs through the 32-bit instantiation from the same
+// state and random streams: the results are those of a 32-bit run.  The
 // launcher picks QB and GEN from the largest cell and the listed tissues.
 #pragma once
+#include <type_traits>
+
 #include "tissue_dev.cuh"
 
 namespace tsg {
@@ -74,8 +81,8 @@ __device__ __forceinline__ uint32_t dir_mask(int v, const Seg& s) {
 }
 
 // Total propensity of voxel v (see voxel_total in k_chi.cu; same value).
-template <bool GEN>
-__device__ __forceinline__ uint64_t seg_voxel_total(const int32_t* cnt, int vmax, int v,
+template <bool GEN, typename CT>
+__device__ __forceinline__ uint64_t seg_voxel_total(const CT* cnt, int vmax, int v,
                                                     const Seg& s, const QRates& q, bool pm,
                                                     bool& ovf, bool& oob) {
   const int vi = static_cast<int>(TSG_IDX(v, vmax, oob));
@@ -153,13 +160,19 @@ __device__ __forceinline__ uint64_t chan_cum(const ChanLane& c, const LaneK& k, 
          k.k17 * X;
 }
 
-template <int H, bool PRE, bool QB, int GEN>
+// items[0 .. n) are the work (n = *n_items_dev when that is given, else
+// n_items); NARROW appends the cells it gives up on to redo[*redo_n ...].
+template <int H, bool PRE, bool QB, int GEN, bool NARROW>
 __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
                                                  const TissueView* __restrict__ views,
                                                  const uint2* __restrict__ items,
                                                  const uint32_t n_items, uint32_t* counter,
                                                  const uint32_t seg_bytes,
-                                                 const uint32_t step_off, const double dt) {
+                                                 const uint32_t step_off, const double dt,
+                                                 uint2* __restrict__ redo, uint32_t* redo_n,
+                                                 const uint32_t* n_items_dev) {
+  static_assert(!NARROW || (PRE && GEN == 0), "16-bit counts: prefix layout, Notch-Delta only");
+  using CT = typename std::conditional<NARROW, uint16_t, int32_t>::type;
   constexpr int G = 32 / H;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -168,10 +181,10 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
   const unsigned segmask = H == 32 ? kFull : (kSegBits << (H * seg));
   unsigned char* base = smem + static_cast<size_t>(wib * G + seg) * seg_bytes;
   TissueView* sv = reinterpret_cast<TissueView*>(base);
-  constexpr int kBytesPerVoxel = PRE ? 20 : 12;
+  constexpr int kBytesPerVoxel = (PRE ? 8 : 0) + 3 * static_cast<int>(sizeof(CT));
   const int vmax = static_cast<int>((seg_bytes - kViewBytes) / kBytesPerVoxel);
   uint64_t* pre = reinterpret_cast<uint64_t*>(base + kViewBytes);  // used only if PRE
-  int32_t* cnt = reinterpret_cast<int32_t*>(base + kViewBytes + (PRE ? 8 * vmax : 0));
+  CT* cnt = reinterpret_cast<CT*>(base + kViewBytes + (PRE ? 8 * vmax : 0));
   const ChanLane cl = chan_lane(sl);
   const ChanLane cl2 = chan_lane(sl + H);  // second channel of each lane when H = 8
   LaneK lk{}, lk2{};                         // their coefficients for the current cell
@@ -180,7 +193,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
   bool have = false, done = false, pm = false;
   bool oob = false;  // checked build: an index out of range (see TSG_IDX)
   Seg s{0, 2, 1, 0, 1, 0, 0};
-  uint32_t cell = 0, step = 0, word3 = 0, key0 = 0, key1 = 0, e = 0, e0 = 0;
+  uint32_t cell = 0, vidx = 0, step = 0, word3 = 0, key0 = 0, key1 = 0, e = 0, e0 = 0;
   uint64_t A = 0, P = 0, Em = 0, Rb = 0, Em2 = 0, Rb2 = 0;
   int Ek = -1, Ek2 = -1, err = 0;
   bool next_ok = false;  // the draws of events e0+H+sl are in Em2/Ek2/Rb2
@@ -193,11 +206,12 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
       uint32_t it = 0;
       if (sl == 0) it = atomicAdd(counter, 1u);
       it = __shfl_sync(segmask, it, 0, H);
-      if (it >= n_items) {
+      if (it >= (n_items_dev ? *n_items_dev : n_items)) {
         done = true;
       } else {
         const uint2 w = items ? items[it] : make_uint2(0u, it);
         cell = w.y;
+        vidx = w.x;
         const uint64_t* src = reinterpret_cast<const uint64_t*>(views + w.x);
         uint64_t* dst = reinterpret_cast<uint64_t*>(sv);
         for (int i = sl; i < static_cast<int>(sizeof(TissueView) / 8); i += H) dst[i] = src[i];
@@ -223,16 +237,32 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
           __syncwarp(segmask);
         } else {
           g = sv->counts + static_cast<size_t>(cell) * 3 * s.V;
+          bool big = false;  // NARROW: a count above 65535 (the cell goes to the redo list)
           if ((s.V & 3) == 0) {
             const int V4 = s.V >> 2;
             for (int sp = 0; sp < 3; ++sp) {
               const int4* a = reinterpret_cast<const int4*>(g + sp * s.V);
-              int4* b = reinterpret_cast<int4*>(cnt + sp * vmax);
-              for (int i = sl; i < V4; i += H) b[i] = a[i];
+              if (NARROW) {
+                uint2* b = reinterpret_cast<uint2*>(cnt + sp * vmax);
+                for (int i = sl; i < V4; i += H) {
+                  const int4 x = a[i];
+                  const uint32_t x0 = static_cast<uint32_t>(x.x), x1 = static_cast<uint32_t>(x.y);
+                  const uint32_t x2 = static_cast<uint32_t>(x.z), x3 = static_cast<uint32_t>(x.w);
+                  big |= (x0 | x1 | x2 | x3) > 0xFFFFu;
+                  b[i] = make_uint2((x0 & 0xFFFFu) | (x1 << 16), (x2 & 0xFFFFu) | (x3 << 16));
+                }
+              } else {
+                int4* b = reinterpret_cast<int4*>(cnt + sp * vmax);
+                for (int i = sl; i < V4; i += H) b[i] = a[i];
+              }
             }
           } else {
             for (int sp = 0; sp < 3; ++sp)
-              for (int i = sl; i < s.V; i += H) cnt[sp * vmax + i] = g[sp * s.V + i];
+              for (int i = sl; i < s.V; i += H) {
+                const int32_t x = g[sp * s.V + i];
+                if (NARROW) big |= static_cast<uint32_t>(x) > 0xFFFFu;
+                cnt[sp * vmax + i] = static_cast<CT>(x);
+              }
           }
           __syncwarp(segmask);
           step = *sv->step + step_off;
@@ -263,10 +293,11 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
           e0 = 0;
           draw_event(e0 + sl, step, cell, word3, key0, key1, Em, Ek, Rb);
           next_ok = false;
-          err = bad_qb                         ? kErrInternal
-                : __any_sync(segmask, bad_state) ? kErrState
-                : __any_sync(segmask, ovf)       ? kErrOverflow
-                                                 : 0;
+          err = (NARROW && __any_sync(segmask, big)) ? kErrNarrow
+                : bad_qb                            ? kErrInternal
+                : __any_sync(segmask, bad_state)    ? kErrState
+                : __any_sync(segmask, ovf)          ? kErrOverflow
+                                                    : 0;
           have = true;
           __syncwarp(segmask);
         }
@@ -442,10 +473,10 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
       const int dd = sl == 0 ? dd0 : sl == 1 ? dd1 : dd2;
       const int xv = (sl == 1 && hop) ? u : v;
       if (dd != 0) {
-        int32_t* c = &cnt[TSG_IDX(sp * vmax + xv, 3 * vmax, oob)];
-        const int nv = *c + dd;
-        *c = nv;
-        if (nv > kCountMax) err |= kErrOverflow;
+        CT* c = &cnt[TSG_IDX(sp * vmax + xv, 3 * vmax, oob)];
+        const int nv = static_cast<int>(*c) + dd;
+        *c = static_cast<CT>(nv);
+        if (nv > (NARROW ? 0xFFFF : kCountMax)) err |= NARROW ? kErrNarrow : kErrOverflow;
       }
     }
     __syncwarp();
@@ -522,23 +553,38 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     const unsigned seg_err = (__ballot_sync(kFull, err != 0) >> (seg * H)) & kSegBits;
     const bool finish = act && (!fire_ok || seg_err != 0u);
     if (finish) {
-      if ((s.V & 3) == 0) {
-        const int V4 = s.V >> 2;
-        for (int sp = 0; sp < 3; ++sp) {
-          int4* a = reinterpret_cast<int4*>(g + sp * s.V);
-          const int4* b = reinterpret_cast<const int4*>(cnt + sp * vmax);
-          for (int i = sl; i < V4; i += H) a[i] = b[i];
-        }
+      if (NARROW && __any_sync(segmask, (err & kErrNarrow) != 0)) {
+        // a count passed 65535: the cell stays as it was, for the 32-bit pass
+        if (sl == 0) redo[atomicAdd(redo_n, 1u)] = make_uint2(vidx, cell);
       } else {
-        for (int sp = 0; sp < 3; ++sp)
-          for (int i = sl; i < s.V; i += H) g[sp * s.V + i] = cnt[sp * vmax + i];
-      }
-      const int e_or = static_cast<int>(__reduce_or_sync(segmask, static_cast<unsigned>(err)));
-      if (sl == 0) {
-        sv->ev_last[cell] = e;
-        sv->t_last[cell] = tnow;
-        sv->ev_total[cell] += e;
-        if (e_or) atomicOr(sv->err, e_or);
+        if ((s.V & 3) == 0) {
+          const int V4 = s.V >> 2;
+          for (int sp = 0; sp < 3; ++sp) {
+            int4* a = reinterpret_cast<int4*>(g + sp * s.V);
+            if (NARROW) {
+              const uint2* b = reinterpret_cast<const uint2*>(cnt + sp * vmax);
+              for (int i = sl; i < V4; i += H) {
+                const uint2 x = b[i];
+                a[i] = make_int4(static_cast<int>(x.x & 0xFFFFu), static_cast<int>(x.x >> 16),
+                                 static_cast<int>(x.y & 0xFFFFu), static_cast<int>(x.y >> 16));
+              }
+            } else {
+              const int4* b = reinterpret_cast<const int4*>(cnt + sp * vmax);
+              for (int i = sl; i < V4; i += H) a[i] = b[i];
+            }
+          }
+        } else {
+          for (int sp = 0; sp < 3; ++sp)
+            for (int i = sl; i < s.V; i += H)
+              g[sp * s.V + i] = static_cast<int32_t>(cnt[sp * vmax + i]);
+        }
+        const int e_or = static_cast<int>(__reduce_or_sync(segmask, static_cast<unsigned>(err)));
+        if (sl == 0) {
+          sv->ev_last[cell] = e;
+          sv->t_last[cell] = tnow;
+          sv->ev_total[cell] += e;
+          if (e_or) atomicOr(sv->err, e_or);
+        }
       }
       err = 0;
       have = false;

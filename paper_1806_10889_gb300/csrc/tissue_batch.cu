@@ -41,7 +41,8 @@ struct tissue_batch {
   unsigned char* dmem = nullptr;
   TissueView* d_views = nullptr;
   uint2* d_items = nullptr;   // chi items of every class, then x-faces, then y-faces
-  uint32_t* d_counters = nullptr;
+  uint32_t* d_counters = nullptr;  // per class: work counter, redo count, redo-pass work counter
+  uint2* d_redo = nullptr;         // cells a class's 16-bit-count pass gives up on
   size_t xface_off = 0, yface_off = 0, wm_off = 0;
   uint32_t n_xfaces = 0, n_yfaces = 0;
   uint32_t n_wm = 0, wm_vmax = 0;  // well-mixed cells of all members (one launch)
@@ -59,11 +60,13 @@ int chi_all(tissue_batch* b, double dt) {
     return TISSUE_E_CUDA;
   for (size_t c = 0; c < b->classes.size(); ++c) {
     const ClassPlan& p = b->classes[c];
-    if (cudaMemsetAsync(b->d_counters + c, 0, sizeof(uint32_t), b->stream) != cudaSuccess)
+    uint32_t* counters = b->d_counters + 3 * c;
+    if (cudaMemsetAsync(counters, 0, 3 * sizeof(uint32_t), b->stream) != cudaSuccess)
       return TISSUE_E_CUDA;
-    if (launch_chi_seg(b->d_views, b->d_items + p.items_off, p.n_items, b->d_counters + c, p.V,
+    const ChiRedo redo{b->d_redo, counters};
+    if (launch_chi_seg(b->d_views, b->d_items + p.items_off, p.n_items, counters, p.V,
                        static_cast<int>(p.lanes), static_cast<int>(p.warps_per_block), 0, 0u, dt,
-                       p.layout == TISSUE_LAYOUT_PREFIX, p.gen, b->stream) != cudaSuccess)
+                       p.layout == TISSUE_LAYOUT_PREFIX, p.gen, &redo, b->stream) != cudaSuccess)
       return TISSUE_E_CUDA;
   }
   return TISSUE_OK;
@@ -173,7 +176,11 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
 
   const size_t views_bytes = (sizeof(TissueView) * count + 255) & ~static_cast<size_t>(255);
   const size_t items_bytes = (sizeof(uint2) * items.size() + 255) & ~static_cast<size_t>(255);
-  const size_t total = views_bytes + items_bytes + sizeof(uint32_t) * b->classes.size();
+  size_t redo_items = 0;  // the classes run one after another and share the redo list
+  for (const ClassPlan& p : b->classes) redo_items = std::max<size_t>(redo_items, p.n_items);
+  const size_t redo_bytes = (sizeof(uint2) * redo_items + 255) & ~static_cast<size_t>(255);
+  const size_t total =
+      views_bytes + items_bytes + redo_bytes + 3 * sizeof(uint32_t) * b->classes.size();
   if (lib_malloc(reinterpret_cast<void**>(&b->dmem), total) != cudaSuccess) {
     cudaGetLastError();
     delete b;
@@ -181,7 +188,8 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
   }
   b->d_views = reinterpret_cast<TissueView*>(b->dmem);
   b->d_items = reinterpret_cast<uint2*>(b->dmem + views_bytes);
-  b->d_counters = reinterpret_cast<uint32_t*>(b->dmem + views_bytes + items_bytes);
+  b->d_redo = reinterpret_cast<uint2*>(b->dmem + views_bytes + items_bytes);
+  b->d_counters = reinterpret_cast<uint32_t*>(b->dmem + views_bytes + items_bytes + redo_bytes);
   std::vector<TissueView> views(count);
   for (uint32_t i = 0; i < count; ++i) views[i] = info[i].view;
   // Members' pending work (creation, earlier steps) must finish before the

@@ -19,6 +19,9 @@ constexpr int kErrEventIndex = 2;
 constexpr int kErrInternal = 4;  // a selection invariant failed (never expected)
 constexpr int kErrState = 8;     // promoter model: more bound sites than sites in a voxel
 constexpr int kErrBounds = 16;   // checked build: an array index was out of range
+// 16-bit counts: a count passed 65535 and the cell is redone with 32-bit
+// counts (never reported; the launcher handles it).
+constexpr int kErrNarrow = 32;
 constexpr uint32_t kModelND = 0u;        // Hill-repressed Notch-Delta lattice model
 constexpr uint32_t kModelPromoter = 1u;  // the paper's promoter model (Sec. III-A1)
 constexpr int kCountMax = (1 << 30) - 1;      // largest count a voxel may hold
@@ -105,16 +108,28 @@ cudaError_t launch_chi(const TissueView& t, uint32_t step_off, double dt, int wa
 // gen: the models of the listed tissues: 0 Notch-Delta only (the fast
 // path), 1 either or a trace is on (each cell tests its tissue's model), 2
 // promoter only.
+// redo: scratch for the 16-bit-count pass, used when the listed cells have
+// more than 256 voxels, gen = 0 and pre (shared memory then bounds how many
+// cells an SM holds): items holds n_items entries, counters three words
+// {work counter of the first pass, redo count, work counter of the 32-bit
+// pass}, all three cleared by the caller before the call (counters[0] is
+// then d_counter).  nullptr: 32-bit counts only.
+struct ChiRedo {
+  uint2* items;
+  uint32_t* counters;
+};
 cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
                            uint32_t* d_counter, uint32_t vmax_cells, int H, int warps_per_block,
                            int blocks, uint32_t step_off, double dt, bool pre, int gen,
-                           cudaStream_t stream);
+                           const ChiRedo* redo, cudaStream_t stream);
 using ChiSegKernel = void (*)(const TissueView*, const uint2*, uint32_t, uint32_t*, uint32_t,
-                              uint32_t, double);
+                              uint32_t, double, uint2*, uint32_t*, const uint32_t*);
 ChiSegKernel chi_seg_kernel_nd(int H, bool pre, bool qb);   // k_chi_seg.cu
 ChiSegKernel chi_seg_kernel_gen(int H, bool pre, bool qb);  // k_chi_seg_gen.cu
 ChiSegKernel chi_seg_kernel_pm(int H, bool pre, bool qb);   // k_chi_seg_pm.cu
-uint32_t seg_bytes_for(uint32_t V, int H, bool pre);
+// 16-bit counts, prefix layout, Notch-Delta only; nullptr where not built.
+ChiSegKernel chi_seg_kernel_narrow(int H, bool qb);          // k_chi_seg_narrow.cu
+uint32_t seg_bytes_for(uint32_t V, int H, bool pre, bool narrow = false);
 // Well-mixed cells (k_chi_wm.cu): one warp per (tissue, cell) item;
 // vmax_cells is the largest V among the listed cells.
 cudaError_t launch_chi_wm(const TissueView* d_views, const uint2* d_items, uint32_t n_items,

@@ -37,7 +37,8 @@ struct tissue {
   tissue_launch cfg{TISSUE_KERNEL_WARP, 32, 4, 0, TISSUE_LAYOUT_PREFIX};
   uint32_t scheme = TISSUE_SPLIT_LIE;
   TissueView* d_view = nullptr;   // device copy of the view, for the persistent kernel
-  uint32_t* d_work = nullptr;     // work-list counter of the persistent kernel
+  uint32_t* d_work = nullptr;     // work-list counters of the persistent kernel (3 words)
+  uint2* d_redo = nullptr;        // cells the 16-bit-count pass gives up on
   uint8_t* d_wm = nullptr;        // per cell: 1 = well-mixed chi
   uint32_t wm_cells = 0;
   std::vector<uint8_t> wm_host;   // host copy of d_wm (empty: no well-mixed cell)
@@ -63,7 +64,8 @@ bool desc_ok(const tissue_desc* d) {
 uint64_t cells_of(const tissue_desc* d) { return static_cast<uint64_t>(d->width) * d->height; }
 
 struct ScratchLayout {
-  size_t hill, ev_last, t_last, ev_total, step, err, view, work, wm, lat_items, wm_items, total;
+  size_t hill, ev_last, t_last, ev_total, step, err, view, work, wm, lat_items, wm_items, redo,
+      total;
 };
 
 ScratchLayout layout(const tissue_desc* d) {
@@ -85,13 +87,15 @@ ScratchLayout layout(const tissue_desc* d) {
   o = up(o + sizeof(int));
   L.view = o;
   o = up(o + sizeof(TissueView));
-  L.work = o;
-  o = up(o + sizeof(uint32_t));
+  L.work = o;  // work counter, redo count, work counter of the 32-bit redo pass
+  o = up(o + 3 * sizeof(uint32_t));
   L.wm = o;
   o = up(o + cells);
   L.lat_items = o;
   o = up(o + sizeof(uint2) * cells);
   L.wm_items = o;
+  o = up(o + sizeof(uint2) * cells);
+  L.redo = o;  // cells the 16-bit-count pass hands to the 32-bit one
   o = up(o + sizeof(uint2) * cells);
   L.total = o;
   return L;
@@ -163,13 +167,14 @@ cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt
       e = launch_chi_wm(t->d_view, t->d_wm_items, t->wm_cells, v.V, i, dt, t->stream);
       if (e != cudaSuccess) return e;
     }
-    e = cudaMemsetAsync(t->d_work, 0, sizeof(uint32_t), t->stream);
+    e = cudaMemsetAsync(t->d_work, 0, 3 * sizeof(uint32_t), t->stream);
     if (e != cudaSuccess) return e;
+    const ChiRedo redo{t->d_redo, t->d_work};
     return launch_chi_seg(t->d_view, t->wm_cells ? t->d_lat_items : nullptr, cells - t->wm_cells,
                           t->d_work, v.V, static_cast<int>(c.lanes_per_cell),
                           static_cast<int>(c.warps_per_block), static_cast<int>(c.blocks), i, dt,
                           c.smem_layout == TISSUE_LAYOUT_PREFIX,
-                          t->q.kind == kModelPromoter ? 2 : t->d_trace != nullptr ? 1 : 0,
+                          t->q.kind == kModelPromoter ? 2 : t->d_trace != nullptr ? 1 : 0, &redo,
                           t->stream);
   }
   return launch_chi(v, i, dt, static_cast<int>(c.warps_per_block), t->stream);
@@ -340,6 +345,7 @@ int tissue_create(const tissue_desc* d, void* dev_counts, size_t bytes, void* cu
   t->d_err = reinterpret_cast<int*>(t->scratch + L.err);
   t->d_view = reinterpret_cast<TissueView*>(t->scratch + L.view);
   t->d_work = reinterpret_cast<uint32_t*>(t->scratch + L.work);
+  t->d_redo = reinterpret_cast<uint2*>(t->scratch + L.redo);
   t->d_wm = reinterpret_cast<uint8_t*>(t->scratch + L.wm);
   t->d_lat_items = reinterpret_cast<uint2*>(t->scratch + L.lat_items);
   t->d_wm_items = reinterpret_cast<uint2*>(t->scratch + L.wm_items);

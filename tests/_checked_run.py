@@ -21,10 +21,12 @@ from tests._util import orc_desc, orc_model  # noqa: E402
 P, PRE, REC = T.KERNEL_PERSISTENT, T.LAYOUT_PREFIX, T.LAYOUT_RECOMPUTE
 
 
-def same(spec, dt, n_steps, config=None, scheme=O.LIE):
+def same(spec, dt, n_steps, config=None, scheme=O.LIE, x0=None):
     d, m = orc_desc(spec), orc_model(spec)
-    ref = O.init_counts(d)
+    ref = O.init_counts(d) if x0 is None else x0.copy()
     g = T.Tissue(spec)
+    if x0 is not None:
+        g.write_counts(x0, 0)
     if config:
         g.set_launch_config(*config)
     if scheme == O.STRANG:
@@ -55,6 +57,15 @@ def main():
             except T.TissueError as e:
                 if e.code != T.E_ARG:  # E_ARG: shape does not fit shared memory
                     raise
+    # 32x32-voxel cells with 16-bit counts: one cell starts above 65535 and one
+    # passes it mid-step, so both go through the 32-bit redo pass
+    big = TissueSpec(3, 2, 32, seed=71, tissue_id=3).with_model(hopD=0.0, k_off=1.0, k_in=0.0)
+    x = O.init_counts(orc_desc(big)).reshape(big.cells, 3, big.V)
+    x[1, 0, 0] = 70000
+    x[4, 0, 5] = 65000
+    x[4, 2, 5] = 0xFFFF
+    for cfg in (None, (P, 16, 2, 0, PRE), (P, 8, 2, 0, PRE)):
+        same(big, 0.05, 2, cfg, x0=x.ravel())
     model = W.promoter_model(8)
     model["kd"] = 3.0
     pm = TissueSpec(4, 3, 8, seed=7, init_lambda=(0.6, 0.4, 0.0), model=model)

@@ -83,6 +83,11 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
+            # nvidia-smi's start-up (driver and NVML initialisation) must not
+            # overlap the timed launches: wait for its first sample
+            t0 = time.perf_counter()
+            while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -255,6 +260,17 @@ def run_ours(args, rank, world, local_rank):
                     "traffic": args.chi_traffic, "kernel": "k_chi",
                     "peak_source": f"{peak_kind} hbm_gbs"}
 
+    # our kernels per step: chi, both face phases, the step counter.  Cells of
+    # more than 256 voxels (Notch-Delta, persistent prefix layout) add the
+    # 32-bit redo pass of the 16-bit-count chi launch; a tissue that fits one
+    # wave of the 16-lane launch (152 SMs x 5 blocks x 8 cells) runs chi as
+    # the heavy/light split (partition kernel + two launches)
+    persistent_pre = launch[0] == 1 and launch[4] == 0
+    narrow = persistent_pre and spec.V > 256 and "kind" not in spec.model
+    split = (persistent_pre and launch[1] == 16 and launch[2] == 4 and launch[3] == 0
+             and spec.V <= 256 and 1024 < spec.cells <= 152 * 5 * 8
+             and spec.fidelity == "lattice")
+    launches_per_step = 4 + int(narrow) + 2 * int(split) + int(spec.fidelity != "lattice")
     out = {
         "metric": METRIC if args.workload == "medium" else f"SSA events/s, {args.workload} tissue",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -275,8 +291,9 @@ def run_ours(args, rank, world, local_rank):
         "events_per_step": events_job / args.steps,
         "chi_events_per_step": chi_events / args.steps,
         "chi_ms_per_step": chi_ms / args.steps, "sig_ms_per_step": sig_ms / args.steps,
+        "step_ms_median": statistics.median(step_ms), "step_ms_max": max(step_ms),
         "e2e": e2e,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
         "clocks": clocks.summary(),
         "wall_s_timed": wall,

@@ -260,17 +260,11 @@ def run_ours(args, rank, world, local_rank):
                     "traffic": args.chi_traffic, "kernel": "k_chi",
                     "peak_source": f"{peak_kind} hbm_gbs"}
 
-    # our kernels per step: chi, both face phases, the step counter.  Cells of
+    # our kernels per step: chi, both face phases, the step counter; cells of
     # more than 256 voxels (Notch-Delta, persistent prefix layout) add the
-    # 32-bit redo pass of the 16-bit-count chi launch; a tissue that fits one
-    # wave of the 16-lane launch (152 SMs x 5 blocks x 8 cells) runs chi as
-    # the heavy/light split (partition kernel + two launches)
-    persistent_pre = launch[0] == 1 and launch[4] == 0
-    narrow = persistent_pre and spec.V > 256 and "kind" not in spec.model
-    split = (persistent_pre and launch[1] == 16 and launch[2] == 4 and launch[3] == 0
-             and spec.V <= 256 and 1024 < spec.cells <= 152 * 5 * 8
-             and spec.fidelity == "lattice")
-    launches_per_step = 4 + int(narrow) + 2 * int(split) + int(spec.fidelity != "lattice")
+    # 32-bit redo pass of the 16-bit-count chi launch
+    narrow = launch[0] == 1 and launch[4] == 0 and spec.V > 256 and "kind" not in spec.model
+    launches_per_step = 4 + int(narrow) + int(spec.fidelity != "lattice")
     out = {
         "metric": METRIC if args.workload == "medium" else f"SSA events/s, {args.workload} tissue",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

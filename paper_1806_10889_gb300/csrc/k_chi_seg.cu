@@ -48,11 +48,7 @@ cudaError_t launch_one(ChiSegKernel k, const TissueView* d_views, const uint2* d
                        cudaStream_t stream) {
   const size_t smem = static_cast<size_t>(warps_per_block) * (32 / H) * seg_bytes;
   const int threads = 32 * warps_per_block;
-  // all of an SM's unified memory as shared memory, for every instantiation:
-  // two chi launches then share SMs without waiting for a carveout change
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                       cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   if (smem > 48 * 1024)
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -105,98 +101,6 @@ cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint
   if (e != cudaSuccess) return e;
   return launch_one(k, d_views, redo->items, n_items, redo->counters + 1, redo->counters + 2,
                     seg_bytes, H, warps_per_block, blocks, step_off, dt, nullptr, nullptr, stream);
-}
-
-namespace {
-
-// Heavy/light partition of one tissue's cells by their last chi event counts
-// (a cell is heavy when its count exceeds 33/32 of the mean; at most `cap`
-// cells, the heavy launch's segments, are heavy: the rest stay light so that
-// no heavy cell waits for a segment), one block.  It also clears the two
-// launches' work counters: counts = {heavy cells, light cells, heavy work
-// counter, light work counter}.
-__global__ void __launch_bounds__(1024) k_split_cells(const uint64_t* __restrict__ ev_last,
-                                                      uint32_t cells, uint32_t cap, uint2* heavy,
-                                                      uint2* light, uint32_t* counts) {
-  __shared__ unsigned long long part[32];
-  __shared__ uint32_t nh, nl;
-  if (threadIdx.x == 0) nh = nl = 0u;
-  unsigned long long sum = 0;
-  for (uint32_t c = threadIdx.x; c < cells; c += blockDim.x) sum += ev_last[c];
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(kFull, sum, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    unsigned long long w = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0ull;
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(kFull, w, o);
-    if (threadIdx.x == 0) part[0] = w;
-  }
-  __syncthreads();
-  sum = part[0];
-  // exact in 64 bits: cells <= 2^16 and a cell's events per step < 2^32
-  for (uint32_t c = threadIdx.x; c < cells; c += blockDim.x) {
-    const uint32_t h = 32ull * cells * ev_last[c] > 33ull * sum ? atomicAdd(&nh, 1u) : cap;
-    if (h < cap)
-      heavy[h] = make_uint2(0u, c);
-    else
-      light[atomicAdd(&nl, 1u)] = make_uint2(0u, c);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    counts[0] = nh < cap ? nh : cap;
-    counts[1] = nl;
-    counts[2] = 0u;
-    counts[3] = 0u;
-  }
-}
-
-}  // namespace
-
-bool chi_split_fits(uint32_t V, int H, int warps_per_block, uint32_t cells, int gen) {
-  if (H != 16 || V > 256 || cells > 65536u || gen == 1) return false;
-  const ChiSegKernel k = gen == 2 ? chi_seg_kernel_pm(16, true, false) : chi_seg_kernel_nd(16, true, false);
-  const size_t smem =
-      static_cast<size_t>(warps_per_block) * 2 * seg_bytes_for(V, 16, true);
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem)) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * warps_per_block, smem) !=
-          cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  // one wave: every cell has a segment from the start
-  return static_cast<uint64_t>(cells) <= static_cast<uint64_t>(sms) * per_sm * warps_per_block * 2;
-}
-
-cudaError_t launch_chi_seg_split(const TissueView* d_view, const uint64_t* ev_last, uint32_t cells,
-                                 uint2* heavy_items, uint2* light_items, uint32_t* counters,
-                                 uint32_t V, int warps_per_block, uint32_t step_off, double dt,
-                                 int gen, cudaStream_t stream, cudaStream_t side, cudaEvent_t fork,
-                                 cudaEvent_t join) {
-  if (cells == 0) return cudaSuccess;
-  // heavy cells, one per warp, on a grid of cells/8 segments (2 per block)
-  const uint32_t heavy_cap = cells / 8 > 0 ? cells / 8 : 1;
-  k_split_cells<<<1, 1024, 0, stream>>>(ev_last, cells, heavy_cap, heavy_items, light_items,
-                                        counters);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const ChiSegKernel k32 = gen == 2 ? chi_seg_kernel_pm(32, true, false) : chi_seg_kernel_nd(32, true, false);
-  const ChiSegKernel k16 = gen == 2 ? chi_seg_kernel_pm(16, true, false) : chi_seg_kernel_nd(16, true, false);
-  if ((e = cudaEventRecord(fork, stream)) != cudaSuccess ||
-      (e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess)
-    return e;
-  e = launch_one(k32, d_view, heavy_items, heavy_cap, counters, counters + 2,
-                 seg_bytes_for(V, 32, true), 32, 2, 0, step_off, dt, nullptr, nullptr, side);
-  if (e != cudaSuccess) return e;
-  if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
-  e = launch_one(k16, d_view, light_items, cells, counters + 1, counters + 3,
-                 seg_bytes_for(V, 16, true), 16, warps_per_block, 0, step_off, dt, nullptr,
-                 nullptr, stream);
-  if (e != cudaSuccess) return e;
-  return cudaStreamWaitEvent(stream, join, 0);
 }
 
 }  // namespace tsg

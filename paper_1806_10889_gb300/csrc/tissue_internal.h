@@ -130,21 +130,6 @@ ChiSegKernel chi_seg_kernel_pm(int H, bool pre, bool qb);   // k_chi_seg_pm.cu
 // 16-bit counts, prefix layout, Notch-Delta only; nullptr where not built.
 ChiSegKernel chi_seg_kernel_narrow(int H, bool qb);          // k_chi_seg_narrow.cu
 uint32_t seg_bytes_for(uint32_t V, int H, bool pre, bool narrow = false);
-// The heavy/light split of one tissue's chi (k_chi_seg.cu): whether its
-// cells fit one wave of the 16-lane prefix launch (gen 0 or 2, V <= 256);
-// then a one-block kernel puts the cells whose last step's chi events
-// (ev_last[cell]) exceed 33/32 of the mean in heavy_items, the others in
-// light_items, with the counts and work counters in counters[0..3]; the heavy
-// cells run with 32 lanes on `side` (forked from and joined back to `stream`
-// by the two events), the light ones with 16 lanes on `stream`.  The split
-// changes no result: every cell's trajectory is independent of which
-// segment runs it.
-bool chi_split_fits(uint32_t V, int H, int warps_per_block, uint32_t cells, int gen);
-cudaError_t launch_chi_seg_split(const TissueView* d_view, const uint64_t* ev_last, uint32_t cells,
-                                 uint2* heavy_items, uint2* light_items, uint32_t* counters,
-                                 uint32_t V, int warps_per_block, uint32_t step_off, double dt,
-                                 int gen, cudaStream_t stream, cudaStream_t side, cudaEvent_t fork,
-                                 cudaEvent_t join);
 // Well-mixed cells (k_chi_wm.cu): one warp per (tissue, cell) item;
 // vmax_cells is the largest V among the listed cells.
 cudaError_t launch_chi_wm(const TissueView* d_views, const uint2* d_items, uint32_t n_items,

@@ -37,7 +37,7 @@ struct tissue {
   tissue_launch cfg{TISSUE_KERNEL_WARP, 32, 4, 0, TISSUE_LAYOUT_PREFIX};
   uint32_t scheme = TISSUE_SPLIT_LIE;
   TissueView* d_view = nullptr;   // device copy of the view, for the persistent kernel
-  uint32_t* d_work = nullptr;     // work-list counters of the persistent kernel (4 words)
+  uint32_t* d_work = nullptr;     // work-list counters of the persistent kernel (3 words)
   uint2* d_redo = nullptr;        // cells the 16-bit-count pass gives up on
   uint8_t* d_wm = nullptr;        // per cell: 1 = well-mixed chi
   uint32_t wm_cells = 0;
@@ -47,10 +47,6 @@ struct tissue {
   TraceRec* d_trace = nullptr;    // event trace (tissue_trace_begin); nullptr when off
   uint32_t* d_trace_len = nullptr;
   uint32_t trace_cap = 0;
-  // the second stream and its fork/join events of the heavy/light chi split
-  // (created on first use)
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -91,8 +87,8 @@ ScratchLayout layout(const tissue_desc* d) {
   o = up(o + sizeof(int));
   L.view = o;
   o = up(o + sizeof(TissueView));
-  L.work = o;  // work counter, redo count, redo-pass work counter; or the split's four
-  o = up(o + 4 * sizeof(uint32_t));
+  L.work = o;  // work counter, redo count, work counter of the 32-bit redo pass
+  o = up(o + 3 * sizeof(uint32_t));
   L.wm = o;
   o = up(o + cells);
   L.lat_items = o;
@@ -171,29 +167,15 @@ cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt
       e = launch_chi_wm(t->d_view, t->d_wm_items, t->wm_cells, v.V, i, dt, t->stream);
       if (e != cudaSuccess) return e;
     }
-    const int gen = t->q.kind == kModelPromoter ? 2 : t->d_trace != nullptr ? 1 : 0;
-    // A tissue that fits one wave of the default 16-lane launch: the step
-    // ends with its slowest cells' event chains, so the cells that had more
-    // than 33/32 of the mean events last step run one per warp (a shorter
-    // chain) on a second stream while the rest run two per warp.
-    if (!t->wm_cells && c.smem_layout == TISSUE_LAYOUT_PREFIX && c.lanes_per_cell == 16 &&
-        c.blocks == 0 && cells > kFewCells &&
-        chi_split_fits(v.V, 16, static_cast<int>(c.warps_per_block), cells, gen)) {
-      if (!t->side && (cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking) != cudaSuccess ||
-                       cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming) != cudaSuccess ||
-                       cudaEventCreateWithFlags(&t->join, cudaEventDisableTiming) != cudaSuccess))
-        return cudaGetLastError();
-      return launch_chi_seg_split(t->d_view, t->ev_last, cells, t->d_lat_items, t->d_redo,
-                                  t->d_work, v.V, static_cast<int>(c.warps_per_block), i, dt, gen,
-                                  t->stream, t->side, t->fork, t->join);
-    }
     e = cudaMemsetAsync(t->d_work, 0, 3 * sizeof(uint32_t), t->stream);
     if (e != cudaSuccess) return e;
     const ChiRedo redo{t->d_redo, t->d_work};
     return launch_chi_seg(t->d_view, t->wm_cells ? t->d_lat_items : nullptr, cells - t->wm_cells,
                           t->d_work, v.V, static_cast<int>(c.lanes_per_cell),
                           static_cast<int>(c.warps_per_block), static_cast<int>(c.blocks), i, dt,
-                          c.smem_layout == TISSUE_LAYOUT_PREFIX, gen, &redo, t->stream);
+                          c.smem_layout == TISSUE_LAYOUT_PREFIX,
+                          t->q.kind == kModelPromoter ? 2 : t->d_trace != nullptr ? 1 : 0, &redo,
+                          t->stream);
   }
   return launch_chi(v, i, dt, static_cast<int>(c.warps_per_block), t->stream);
 }
@@ -658,12 +640,6 @@ int tissue_trace_end(tissue* t) {
 void tissue_destroy(tissue* t) {
   if (!t) return;
   cudaStreamSynchronize(t->stream);
-  if (t->side) {
-    cudaStreamSynchronize(t->side);
-    cudaStreamDestroy(t->side);
-  }
-  if (t->fork) cudaEventDestroy(t->fork);
-  if (t->join) cudaEventDestroy(t->join);
   if (t->d_trace_len) cudaFree(t->d_trace_len);
   cudaFree(t->scratch);
   delete t;

@@ -290,8 +290,10 @@ void tissue_batch_destroy(tissue_batch* b);
  * Runs n_steps steps exactly as tissue_step would, on cuda_stream, and waits
  * for them; returns TISSUE_E_ARG if width*height > TISSUE_NOALLOC_MAX_CELLS
  * or an argument is invalid, TISSUE_E_OVERFLOW as tissue_read_counts would.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * n_steps == 0 leaves the state and both outputs untouched, as tissue_step
+ * does.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), also when n_steps == 0; make that first call before
+ * any stream capture.
  * All calls share the one array: calls whose work overlaps on a device race. */
 int tissue_step_noalloc(const tissue_desc* desc, const tissue_model* model, int32_t* dev_counts,
                         uint32_t step_index, double dt, uint32_t n_steps,

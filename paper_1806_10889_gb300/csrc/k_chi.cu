@@ -304,12 +304,14 @@ template <int B>
 cudaError_t launch_chi_b(const TissueView& t, uint32_t step_off, double dt, int wpb,
                          cudaStream_t stream) {
   const size_t smem = static_cast<size_t>(wpb) * 32 * B * 20;
-  static size_t configured = 0;  // largest dynamic shared memory requested so far
-  if (smem > 48 * 1024 && smem > configured) {
+  // The attribute belongs to the current device's copy of the kernel, so it is
+  // set on every launch that needs more than the default 48 KB (a host-side
+  // call, cheap next to the launch): a cache of it would have to be kept per
+  // device and guarded against concurrent callers.
+  if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(k_chi<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   const uint32_t cells = t.width * t.height;
   const uint32_t blocks = (cells + wpb - 1) / wpb;

@@ -83,6 +83,10 @@ extern "C" int tissue_step_noalloc(const tissue_desc* d, const tissue_model* m,
   StaticScratch* s = nullptr;
   int rc = scratch_on_current_device(&s);
   if (rc != TISSUE_OK) return rc;
+  // Like tissue_step, zero steps do nothing: the outputs keep their contents.
+  // The address lookup above has been made, so such a call also serves as the
+  // device's set-up call.
+  if (n_steps == 0) return TISSUE_OK;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
   QRates q{};

@@ -30,25 +30,34 @@ def _noalloc(spec, model, state, step_index, dt, n_steps, ev, tl, stream):
                                        C.c_void_p(tl.data_ptr()), C.c_void_p(stream.cuda_stream))
 
 
-def test_noalloc_matches_tissue_step_on_two_calls_in_a_row():
-    spec = TissueSpec(5, 4, 16, seed=31, tissue_id=9).with_model(k_bind=0.05)
+@pytest.mark.parametrize("n, first_step", [(8, 0), (16, 0), (32, 0), (16, 37)])
+def test_noalloc_matches_tissue_step_on_two_calls_in_a_row(n, first_step):
+    # cells of 8x8, 16x16 and 32x32 voxels (the last needs more than 48 KB of
+    # shared memory per block); one case starts at a global step other than 0
+    spec = TissueSpec(5, 4, n, seed=31, tissue_id=9).with_model(k_bind=0.05)
     dt = 0.1
     ref = T.Tissue(spec)  # the allocating entry points
+    if first_step:
+        ref.write_counts(ref.read_counts(), step_index=first_step)
     state = torch.from_numpy(ref.read_counts()).to("cuda")
     ev = torch.full((3 * spec.cells,), 7, dtype=torch.int64, device="cuda")
     tl = torch.full((3 * spec.cells,), 7.0, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    k = 0
-    for n in (2, 3):  # two calls in a row reuse the same static scratch
-        assert _noalloc(spec, spec.model, state, k, dt, n, ev, tl, stream) == T.OK
-        ref.step(dt, n)
-        k += n
+    k = first_step
+    for steps in (2, 3):  # two calls in a row reuse the same static scratch
+        assert _noalloc(spec, spec.model, state, k, dt, steps, ev, tl, stream) == T.OK
+        ref.step(dt, steps)
+        k += steps
         want = ref.read_counts()
         want_ev, want_tl = ref.read_stats()
         assert np.array_equal(state.cpu().numpy(), want)
         assert np.array_equal(ev.cpu().numpy().astype(np.uint64).reshape(3, -1), want_ev)
         assert np.array_equal(tl.cpu().numpy().view(np.uint64).reshape(3, -1),
                               want_tl.view(np.uint64))
+    # zero steps change nothing, as with tissue_step
+    before = (state.clone(), ev.clone(), tl.clone())
+    assert _noalloc(spec, spec.model, state, k, dt, 0, ev, tl, stream) == T.OK
+    assert all(torch.equal(a, b) for a, b in zip(before, (state, ev, tl)))
     ref.close()
 
 

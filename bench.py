@@ -1,38 +1,52 @@
 """Benchmark of the operator-split tissue SSA on GB300.
 
-One "step" is one Lie splitting step of the whole hot path (chi on every
-cell, then S on every x-face and every y-face) over the benchmark tissue:
-64x64 cells of 16x16 voxels, the Notch-Delta model, dt = 0.1 (the medium
-tissue; synthetic, seeded).  The state is first advanced by an untimed
-burn-in so that the timed steps see molecule counts near their working
-level, then W warm-up steps and K timed steps run.
+Headline (`value`): the uneven 256-tissue batch -- tissue sides drawn from
+2..64 cells, cells of 8x8, 16x16 or 32x32 voxels, D production drawn from
+[5, 20] per tissue, the Notch-Delta model, dt = 0.1 (synthetic, seeded) --
+advanced by the batched path: one persistent chi launch per cell-size class
+and one launch per face phase per step, captured in a CUDA graph, launch
+shapes picked by the autotuner.  One "step" is one Lie splitting step of the
+whole hot path (chi on every cell of every tissue, then S on every x-face and
+every y-face) over all 256 tissues.  The batch is first advanced by an untimed
+burn-in (default 5 time units of the configuration's 20), so the timed steps
+see molecule counts well on their way to their working level; then W warm-up
+and K timed steps run.  The state (about 2 GB) is larger than L2, so no flush
+is needed between steps.
 
 Metric: SSA events per second (all events of chi and both face phases), with
-cell-steps per second beside it.  `value` times the steps with the state
-resident in device memory (CUDA events on the tissue's stream, L2 flushed
-between steps); `e2e` times the same steps through the C ABI with the state
-copied host->device before and device->host after every step.
+cell-steps per second beside it and the plain per-tissue launch (every tissue
+its own tissue_step) from the same state.  `value` times the steps with the
+state resident in device memory (CUDA events on the batch stream); `e2e`
+times batch steps through the C ABI with every tissue's state copied
+host->device before and device->host after every step.  `roofline` is the SM
+issue fraction of the dominant chi launch, from its live CUDA-event time and
+the warp instructions per event ncu measured for that kernel instantiation.
+`cpu_baseline` is the oracle on a sample of member tissues from the same
+state, which must also agree bit for bit with the GPU (`parity_checked`).
 
-Multi-GPU (torchrun, N ranks): every rank advances its own replica tissue
-(tissue_id = rank); there is no data exchange (weak scaling).
+Extra keys: `medium` (64x64 cells of 16x16 voxels, the single-tissue line with
+its own roofline, e2e and oracle check), `large` (256x256 cells of 32x32
+voxels from a burned-in state), `promoter`, `mixed_fidelity` and `serving`
+(p50/p99 latency at a sustainable arrival rate beside saturation throughput).
 
-The serving leg (default: the first 4 requests of the serving workload,
-about a minute) reports p50/p99 latency beside the served events/s.
+Multi-GPU (torchrun, N ranks): every rank advances its own copy of the batch
+(tissue ids offset by rank); there is no data exchange (weak scaling).
 
 `--impl reference` times the CPU oracle (test infrastructure, plain C with
-OpenMP) on a bounded patch of the same workload.
+OpenMP) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
 import sys
 import threading
 import time
+from dataclasses import replace
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -42,20 +56,56 @@ import numpy as np  # noqa: E402
 
 from paper_1806_10889_gb300 import workloads as W  # noqa: E402
 
-METRIC = "SSA events/s (chi + face binding), medium tissue 64x64 cells x 16x16 voxels, dt 0.1"
+METRIC = "SSA events/s (chi + face binding), 256-tissue uneven batch, batched, dt 0.1"
+MEDIUM_METRIC = "SSA events/s (chi + face binding), medium tissue 64x64 cells x 16x16 voxels, dt 0.1"
 UNIT = "events/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # Issue-slot peak of the chip: 152 SMs x 4 schedulers x 1 warp-instruction per
 # clock at the 2070 MHz maximum SM clock.
 ISSUE_PEAK_GINST = 152 * 4 * 2.070
-# Warp instructions the chi kernel executes per chi event on the medium
-# tissue, per launch variant, from ncu (smsp__inst_executed.sum over the 10
-# timed chi launches / their chi events; profiles/k_chi_medium_metrics.md).
-CHI_INST_PER_EVENT = {("persistent", 16, 0): 298.0}
-# DRAM bytes (read + write) per chi launch from the same capture, per variant.
-CHI_TRAFFIC = {("persistent", 16, 0): 1.314e7}
-# Algorithmic DRAM bytes of one chi launch per cell: the state read + write.
-STATE_BYTES_PER_CELL_RW = lambda V: 2 * 3 * V * 4  # noqa: E731
+CSRC = os.path.join(ROOT, "paper_1806_10889_gb300", "csrc")
+# The files that fix the persistent chi kernel's instruction stream.
+CHI_SOURCES = ["chi_seg.cuh", "tissue_dev.cuh", "tissue_internal.h", "k_chi_seg.cu",
+               "k_chi_seg_narrow.cu", "k_chi_seg_gen.cu", "k_chi_seg_pm.cu"]
+# Warp instructions per chi event and DRAM bytes per launch of each
+# instantiation of the persistent chi kernel (lanes per cell, layout, QB, model
+# code, 16-bit counts), measured by ncu (smsp__inst_executed.sum and
+# dram__bytes_{read,write}.sum over the chi launches of the command in
+# profiles/k_chi_inst_per_event_by_cell_size.md, divided by their chi events).
+# `sources` is chi_sources_sha() of the kernel they were measured on: when the
+# kernel changes, the figures are stale and the roofline reports none.
+CHI_IPE = {
+    "sources": None,
+    "kernels": {},
+}
+
+
+def chi_sources_sha() -> str:
+    """SHA-256 over the persistent chi kernel's sources and the nvcc flags."""
+    from paper_1806_10889_gb300.build import NVCC_FLAGS
+    h = hashlib.sha256()
+    for f in CHI_SOURCES:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    h.update(" ".join(x for x in NVCC_FLAGS if not x.startswith("-I")).encode())
+    return h.hexdigest()[:16]
+
+
+def chi_kernel_key(V: int, lanes: int, layout: int, model: str = "nd") -> str:
+    """The instantiation the launcher picks for cells of V voxels."""
+    pre = layout == 0
+    qb = V > lanes * lanes
+    narrow = pre and model == "nd" and V > 256
+    return f"H{lanes}/{'pre' if pre else 'rec'}/qb{int(qb)}/{model}/{'u16' if narrow else 'u32'}"
+
+
+def chi_ipe(workload: str, key: str):
+    """(warp instructions per chi event, DRAM bytes per chi event) of a kernel
+    instantiation on a workload, or None when unmeasured or measured on other
+    kernel sources."""
+    if CHI_IPE["sources"] != chi_sources_sha():
+        return None
+    return CHI_IPE["kernels"].get(f"{workload}:{key}")
 
 
 def _env_rank():
@@ -146,31 +196,340 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def run_ours(args, rank, world, local_rank):
+def _events(tissues) -> np.ndarray:
+    """Cumulative (chi, x-face, y-face) events of each tissue: [len, 3]."""
+    return np.array([t.total_events() for t in tissues], dtype=np.int64).reshape(-1, 3)
+
+
+def _digest(tissues) -> str:
+    h = hashlib.sha256()
+    for t in tissues:
+        h.update(t.read_counts().tobytes())
+    return h.hexdigest()
+
+
+def issue_roofline(workload: str, chi_events: float, chi_ms: float, key: str, V: int,
+                   cells: int, steps: int, launches: int) -> dict:
+    """Issue-bound roofline of one chi launch class: achieved = warp
+    instructions (events x measured instructions per event) per second of its
+    live CUDA-event time.  HBM fraction of the algorithmic state traffic
+    (24 V bytes per cell-step) beside it."""
+    peaks, peak_kind = _peaks()
+    chi_s = chi_ms / 1e3
+    rate = chi_events / chi_s if chi_s > 0 else 0.0
+    hbm = 24 * V * cells * steps / chi_s / 1e9 if chi_s > 0 else 0.0
+    m = chi_ipe(workload, key)
+    out = {"bound": "alu", "unit": "Gwarp-inst/s", "peak": ISSUE_PEAK_GINST,
+           "peak_source": "152 SMs x 4 issue/clk x 2.070 GHz", "kernel": f"k_chi_seg {key}",
+           "chi_events_per_s": rate, "launch_ms": chi_ms / max(launches, 1),
+           "hbm_gbs": hbm, "hbm_frac": hbm / peaks["hbm_gbs"], "hbm_peak_source": peak_kind}
+    if m is None:
+        out.update({"achieved": None, "frac": None, "traffic": None, "inst_per_event": None,
+                    "stale": "no instruction count measured on the current kernel sources"})
+        return out
+    ipe, traffic_per_event = m
+    ach = rate * ipe / 1e9
+    out.update({"achieved": ach, "frac": ach / ISSUE_PEAK_GINST, "inst_per_event": ipe,
+                "traffic": (traffic_per_event * chi_events / max(launches, 1)
+                            if traffic_per_event is not None else None)})
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Headline: the batch
+# ---------------------------------------------------------------------------
+
+def batch_runs(rank: int = 0):
+    runs = W.batch()
+    if rank:
+        runs = [replace(r, tissue=replace(r.tissue, tissue_id=rank * len(runs) + i))
+                for i, r in enumerate(runs)]
+    return runs
+
+
+def oracle_sample(runs, per_class: int = 1, target_cells: int = 256):
+    """Indices of the member tissues the oracle reruns: per cell size, the
+    tissue(s) whose cell count is nearest target_cells (enough cells to keep
+    the host cores busy, few enough to run in seconds)."""
+    pick = []
+    for n in (8, 16, 32):
+        idx = [i for i, r in enumerate(runs) if r.tissue.n == n]
+        idx.sort(key=lambda i: (abs(runs[i].tissue.cells - target_cells), i))
+        pick += idx[:per_class]
+    return sorted(pick)
+
+
+def _orc(spec):
+    import oracle as O
+    d = O.Desc(spec.width, spec.height, spec.n, seed=spec.seed, tissue_id=spec.tissue_id,
+               init_lambda=tuple(spec.init_lambda))
+    return O, d, O.Model(**spec.model)
+
+
+def oracle_check(items, steps: int, dt: float) -> dict:
+    """Rerun each sampled tissue with the oracle from its GPU start state for
+    `steps` steps (all host cores, timed) and compare counts and the last
+    step's statistics bit for bit with the GPU's.
+
+    items: (spec, start counts, start step, gpu counts, gpu n_events, gpu t_last)."""
+    total_ev, total_s, ok, cores, detail = 0, 0.0, True, 1, []
+    for spec, start, step0, g_counts, g_ne, g_tl in items:
+        O, d, m = _orc(spec)
+        counts = np.array(start, dtype=np.int32, copy=True)
+        cores = O.max_threads()
+        t0 = time.perf_counter()
+        ev = 0
+        for k in range(steps):
+            ne, tl = O.step(d, m, counts, step0 + k, 1, dt, n_threads=cores)
+            ev += int(ne.sum())
+        el = time.perf_counter() - t0
+        same = (np.array_equal(counts, g_counts) and np.array_equal(ne, g_ne)
+                and np.array_equal(tl.view(np.uint64), g_tl.view(np.uint64)))
+        ok &= same
+        total_ev += ev
+        total_s += el
+        detail.append({"tissue_id": spec.tissue_id, "cells": spec.cells, "n": spec.n,
+                       "steps": f"{step0}-{step0 + steps - 1}", "events": ev, "bit_exact": same})
+    return {"parity_checked": bool(ok), "events": total_ev, "seconds": total_s, "cores": cores,
+            "tissues": detail}
+
+
+def oracle_single_core(spec, start, step0, dt, cells: int = 32) -> dict:
+    O, d, m = _orc(spec)
+    counts = np.array(start, dtype=np.int32, copy=True)
+    ev, t0 = 0, time.perf_counter()
+    for c in range(min(cells, spec.cells)):
+        ev += O.chi_cell(d, m, counts, c, step0, dt)[0]
+    el = time.perf_counter() - t0
+    return {"value": ev / el, "unit": UNIT, "cores": 1,
+            "sample": f"chi of cells 0-{min(cells, spec.cells) - 1} of tissue {spec.tissue_id} "
+                      f"({spec.n}x{spec.n} voxels) at step {step0}, {ev} events in {el:.2f} s"}
+
+
+def batch_headline(args, rank: int, world: int, dist) -> dict:
     import torch
 
-    from paper_1806_10889_gb300.tissue import DEFAULT_CHI_WPB, Tissue
+    from paper_1806_10889_gb300 import autotune
+    from paper_1806_10889_gb300.batching import Batch
+    from paper_1806_10889_gb300.tissue import Tissue
 
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    runs = batch_runs(rank)
+    dt = runs[0].dt
+    members = [Tissue(r.tissue) for r in runs]
+    torch.cuda.synchronize()
+    bt = Batch(members)
+    burn = int(round(args.batch_burn_in / dt))
+    t_burn = time.perf_counter()
+    if burn:
+        bt.step(dt, burn)
+        bt.sync()
+    t_burn = time.perf_counter() - t_burn
+    tuned = None
+    if args.autotune:
+        tuned = autotune.tune_batch(members, dt, steps=1, max_clones=args.tune_clones)
+        autotune.apply_batch(bt, tuned)
+    # the timed steps replay one step per graph so that each is timed
+    bt.set_schedule(1)
+    bt.set_timing(True)
+    for _ in range(args.warmup):
+        bt.step(dt, 1)
+    bt.sync()
+    classes = bt.classes()
+    step0 = members[0].get_step()
+    sample = oracle_sample(runs, per_class=args.oracle_per_class) if (
+        rank == 0 and world == 1 and not args.no_cpu_baseline) else []
+    starts = {i: members[i].read_counts() for i in sample}
 
-    from dataclasses import replace
-    spec = {"medium": lambda: W.medium(args.dt).tissue,
-            "promoter": lambda: W.promoter().tissue,
-            "mixed": lambda: W.mixed_fidelity().tissue}[args.workload]()
+    ev0 = _events(members)
+    step_ms, class_ms, wm_ms = [], np.zeros(len(classes)), 0.0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(bt.stream)
+            bt.step(dt, 1)
+            b.record(bt.stream)
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+            _, w, cls = bt.read_timing()
+            wm_ms += w
+            class_ms += np.array(cls)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+    bt.sync()
+    ev1 = _events(members)
+    bt.set_timing(False)
+    d_ev = ev1 - ev0
+    events = int(d_ev.sum())
+    total_ms = float(sum(step_ms))
+    total_ms_job, events_job = job_totals(dist, total_ms, float(events))
+    cells = sum(r.tissue.cells for r in runs)
+    after = {i: (members[i].read_counts(), *members[i].read_stats()) for i in sample}
+
+    # per-class chi events and rooflines; the dominant class is the one with
+    # the largest chi time
+    per_class = []
+    for ci, c in enumerate(classes):
+        idx = [i for i, r in enumerate(runs) if r.tissue.V == c["V"]]
+        key = chi_kernel_key(c["V"], c["lanes_per_cell"], c["smem_layout"])
+        rl = issue_roofline("batch", float(d_ev[idx, 0].sum()), float(class_ms[ci]), key, c["V"],
+                            c["cells"], args.steps, args.steps)
+        per_class.append({"V": c["V"], "cells": c["cells"], "tissues": len(idx),
+                          "launch": [c["lanes_per_cell"], c["warps_per_block"], c["smem_layout"]],
+                          "chi_ms_per_step": class_ms[ci] / args.steps,
+                          "chi_events_per_step": float(d_ev[idx, 0].sum()) / args.steps,
+                          "roofline": rl})
+    dom = max(range(len(per_class)), key=lambda i: per_class[i]["chi_ms_per_step"])
+    roofline = dict(per_class[dom]["roofline"])
+    roofline["class_V"] = per_class[dom]["V"]
+
+    # end to end through the C ABI: every tissue's state from pinned host
+    # memory before each step, back to pinned host memory after it
+    e2e = None
+    hosts = [torch.empty(m.spec.state_ints, dtype=torch.int32, pin_memory=True) for m in members]
+    for m, h in zip(members, hosts):
+        m.read_counts_into(h)
+    if args.e2e_steps:
+        k0 = members[0].get_step()
+        e0 = _events(members)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            for m, h in zip(members, hosts):
+                m.write_counts_from(h, step_index=k0 + i)
+            bt.step(dt, 1)
+            bt.sync()
+            for m, h in zip(members, hosts):
+                m.read_counts_into(h)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e_ev = float((_events(members) - e0).sum())
+        e2e_s, e_ev = job_totals(dist, e2e_s, e_ev)
+        nbytes = sum(r.tissue.state_ints * 4 for r in runs)
+        e2e = {"value": e_ev / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+
+    # plain per-tissue launches against the batch, from the same state
+    plain = None
+    if args.plain_steps and rank == 0 and world == 1:
+        k_now = members[0].get_step()
+        clones = [Tissue(r.tissue) for r in runs]
+        for c, h in zip(clones, hosts):
+            c.write_counts_from(h, step_index=k_now)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        p0 = _events(clones)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.plain_steps):
+            for c in clones:
+                c.step(dt, 1)
+        b.record(stream)
+        b.synchronize()
+        plain_ms = a.elapsed_time(b)
+        plain_ev = float((_events(clones) - p0).sum())
+        q0 = _events(members)
+        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a2.record(bt.stream)
+        bt.step(dt, args.plain_steps)
+        b2.record(bt.stream)
+        b2.synchronize()
+        bt.sync()
+        same_ms = a2.elapsed_time(b2)
+        same_ev = float((_events(members) - q0).sum())
+        same = _digest(clones) == _digest(members)
+        plain = {"plain_events_per_s": plain_ev / (plain_ms / 1e3),
+                 "batched_events_per_s": same_ev / (same_ms / 1e3),
+                 "batched_vs_plain": (same_ev / same_ms) / (plain_ev / plain_ms),
+                 "steps": args.plain_steps, "from_step": k_now, "bit_identical": bool(same)}
+        for c in clones:
+            c.close()
+
+    bt.close()
+    for m in members:
+        m.close()
+    del hosts
+
+    cpu = None
+    if sample:
+        items = [(runs[i].tissue, starts[i], step0, *after[i]) for i in sample]
+        chk = oracle_check(items, args.steps, dt)
+        i_big = max(sample, key=lambda i: runs[i].tissue.V)
+        cpu = {"value": chk["events"] / chk["seconds"], "unit": UNIT, "cores": chk["cores"],
+               "kind": "oracle",
+               "sample": f"{len(sample)} member tissues of the batch (one per cell size, "
+                         f"{sum(runs[i].tissue.cells for i in sample)} cells), the {args.steps} "
+                         f"timed steps {step0}-{step0 + args.steps - 1} from the GPU's state, "
+                         f"{chk['events']} events in {chk['seconds']:.2f} s",
+               "parity_checked": chk["parity_checked"], "tissues": chk["tissues"],
+               "single_core": oracle_single_core(runs[i_big].tissue, starts[i_big], step0, dt)}
+
+    out = {
+        "metric": METRIC, "value": events_job / (total_ms_job / 1e3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms_job / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic", "impl": "ours",
+        "config": {"workload": "256 uneven tissues (side U{2..64} cells, cells of 8x8, 16x16 "
+                               "or 32x32 voxels, kD U[5,20]), Notch-Delta model, batched",
+                   "dt": dt, "burn_in_time": args.batch_burn_in, "timed_steps_from": step0,
+                   "config_steps": runs[0].n_steps, "cells": cells, "tissues": len(runs),
+                   "state_bytes": sum(r.tissue.state_ints * 4 for r in runs),
+                   "l2": "state (~2 GB) larger than L2; no flush",
+                   "parallelism": f"replicas x{world}", "graph": "one step per captured graph",
+                   "tuned": None if not tuned else {
+                       "classes": {str(k): list(v) for k, v in tuned["classes"].items()},
+                       "steps_per_graph": tuned["steps_per_graph"]}},
+        "cell_steps_per_s": cells * world * args.steps / (total_ms_job / 1e3),
+        "events_per_step": events_job / args.steps,
+        "chi_events_per_step": float(d_ev[:, 0].sum()) / args.steps,
+        "step_ms_median": statistics.median(step_ms), "step_ms_max": max(step_ms),
+        "sig_ms_per_step": (total_ms - class_ms.sum() - wm_ms) / args.steps,
+        "classes": per_class,
+        "e2e": e2e,
+        "gpu_launches": None,
+        "roofline": roofline,
+        "clocks": clocks.summary(),
+        "wall_s_timed": wall,
+        "burn_in_wall_s": t_burn,
+        "plain": plain,
+        "cpu_baseline": cpu,
+        "parity_checked": None if cpu is None else cpu["parity_checked"],
+    }
+    # our kernels per step: per class the chi launch (and, for cells of more
+    # than 256 voxels with 16-bit counts, its 32-bit redo pass), both face
+    # phases and the step-counter update
+    per_step = sum(1 + int(chi_kernel_key(c["V"], c["lanes_per_cell"], c["smem_layout"])
+                           .endswith("u16")) for c in classes) + 3
+    out["gpu_launches"] = per_step * args.steps
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Single tissues
+# ---------------------------------------------------------------------------
+
+def medium_leg(args) -> dict:
+    """The medium tissue (64x64 cells of 16x16 voxels, dt 0.1) after 20 time
+    units of burn-in: K steps device-timed with the L2 flushed between steps,
+    e2e through the C ABI, its chi roofline, and the oracle rerunning the same
+    K steps from the same state, compared bit for bit."""
+    import torch
+
+    from paper_1806_10889_gb300.tissue import Tissue
+
+    spec = W.medium(args.dt).tissue
     if args.side or args.n:  # profiling cases: same model and seed, other sizes
         spec = replace(spec, width=args.side or spec.width, height=args.side or spec.height,
                        n=args.n or spec.n)
-    if world > 1:  # independent replica per rank
-        spec = replace(spec, tissue_id=rank)
     g = Tissue(spec)
     if args.kernel == "persistent":
         g.set_launch_config(1, args.lanes, args.chi_wpb or 4, 0, args.layout)
-    elif args.kernel == "warp":
-        g.set_launch(args.chi_wpb or DEFAULT_CHI_WPB)
     launch = g.launch_config()
     burn = int(round(args.burn_in / args.dt))
     if burn:
@@ -178,162 +537,102 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         g.step(args.dt, 1)
     g.sync()
-    # the state the timed steps start from, for the CPU baseline (untimed)
-    base_state, base_step = None, 0
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not (args.side or args.n) \
-            and args.workload == "medium":
-        base_state, base_step = g.read_counts(), g.get_step()
+    check = not args.no_cpu_baseline and not (args.side or args.n)
+    base_state, base_step = (g.read_counts(), g.get_step()) if check else (None, g.get_step())
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
-
     ev0 = g.total_events()
     chi_ms = sig_ms = 0.0
     step_ms = []
-    if dist:
-        dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clocks:
-        t_wall = time.perf_counter()
-        for _ in range(args.steps):
-            flush.zero_()  # L2 flush between timed steps (outside the event pair)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            c_ms, s_ms = g.step_timed(args.dt, 1)
-            b.record(stream)
-            b.synchronize()
-            step_ms.append(a.elapsed_time(b))
-            chi_ms += c_ms
-            sig_ms += s_ms
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t_wall
-    ev1 = g.total_events()
-    events = int((ev1 - ev0).sum())
-    chi_events = int(ev1[0] - ev0[0])
-    total_ms = float(sum(step_ms))
-    total_ms_job, events_job = job_totals(dist, total_ms, float(events))
-    value = events_job / (total_ms_job / 1e3)
-    cell_steps = spec.cells * args.steps * world
-
-    # end to end through the C ABI: pinned host state in and out every step
-    e2e = None
-    if not args.no_e2e:
-        host = torch.empty(spec.state_ints, dtype=torch.int32, pin_memory=True)
-        g.read_counts_into(host)
-        e0 = g.total_events()
-        k0 = g.get_step()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            g.write_counts_from(host, step_index=k0 + i)   # H2D of the step's input state
-            g.step(args.dt, 1)
-            g.read_counts_into(host)                       # D2H of the step's result
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        e_ev = float((g.total_events() - e0).sum())
-        e2e_s, e_ev = job_totals(dist, e2e_s, e_ev)
-        nbytes = spec.state_ints * 4
-        e2e = {"value": e_ev / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes}
-
-    peaks, peak_kind = _peaks()
-    chi_s = chi_ms / 1e3
-    chi_rate = chi_events / chi_s if chi_s > 0 else 0.0
-    hbm_achieved = STATE_BYTES_PER_CELL_RW(spec.V) * spec.cells * args.steps / chi_s / 1e9
-    variant = (["warp", "persistent"][launch[0]], launch[1], launch[4])
-    ipe = (CHI_INST_PER_EVENT.get(variant)
-           if not (args.side or args.n) and args.workload == "medium" else None)
-    if ipe:
-        ach = chi_rate * ipe / 1e9
-        roofline = {"bound": "alu", "achieved": ach, "peak": ISSUE_PEAK_GINST,
-                    "unit": "Gwarp-inst/s", "frac": ach / ISSUE_PEAK_GINST,
-                    "traffic": args.chi_traffic or CHI_TRAFFIC.get(variant),
-                    "kernel": f"k_chi ({variant[0]}, {variant[1]} lanes per cell)",
-                    "inst_per_event": ipe,
-                    "hbm_gbs": hbm_achieved, "hbm_frac": hbm_achieved / peaks["hbm_gbs"],
-                    "peak_source": "152 SMs x 4 issue/clk x 2.070 GHz"}
-    else:
-        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": hbm_achieved / peaks["hbm_gbs"],
-                    "traffic": args.chi_traffic, "kernel": "k_chi",
-                    "peak_source": f"{peak_kind} hbm_gbs"}
-
-    # our kernels per step: chi, both face phases, the step counter; cells of
-    # more than 256 voxels (Notch-Delta, persistent prefix layout) add the
-    # 32-bit redo pass of the 16-bit-count chi launch
-    narrow = launch[0] == 1 and launch[4] == 0 and spec.V > 256 and "kind" not in spec.model
-    launches_per_step = 4 + int(narrow) + int(spec.fidelity != "lattice")
-    out = {
-        "metric": METRIC if args.workload == "medium" else f"SSA events/s, {args.workload} tissue",
-        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms_job / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
-        "data": "synthetic", "impl": "ours",
-        "config": {"workload": f"{args.workload if not (args.side or args.n) else 'custom'} "
-                               f"tissue {spec.width}x{spec.height} cells of {spec.n}x{spec.n} "
-                               f"voxels, {'promoter' if 'kind' in spec.model else 'Notch-Delta'}"
-                               f" model, fidelity {spec.fidelity}",
-                   "dt": args.dt, "burn_in_time": args.burn_in, "cells": spec.cells,
-                   "voxels_per_cell": spec.V, "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"replicas x{world}",
-                   "chi_launch": {"kernel": ["warp", "persistent"][launch[0]],
-                                  "lanes_per_cell": launch[1], "warps_per_block": launch[2],
-                                  "smem_layout": ["prefix", "recompute"][launch[4]]}},
-        "cell_steps_per_s": cell_steps / (total_ms_job / 1e3),
-        "events_per_step": events_job / args.steps,
-        "chi_events_per_step": chi_events / args.steps,
-        "chi_ms_per_step": chi_ms / args.steps, "sig_ms_per_step": sig_ms / args.steps,
-        "step_ms_median": statistics.median(step_ms), "step_ms_max": max(step_ms),
-        "e2e": e2e,
-        "gpu_launches": launches_per_step * args.steps,
-        "roofline": roofline,
-        "clocks": clocks.summary(),
-        "wall_s_timed": wall,
-    }
-    g.close()
-    if rank == 0 and world == 1 and not args.no_promoter:
-        out["promoter"] = promoter_leg(args)
-        out["mixed_fidelity"] = promoter_leg(args, W.mixed_fidelity())
-    if rank == 0 and world == 1 and not args.no_batch:
-        out["batched"] = batch_leg(args)
-    if rank == 0 and world == 1 and args.serving:
-        out["serving"] = serving_leg(args)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, base_state, base_step)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
-    return out if rank == 0 else None
-
-
-def promoter_leg(args, run=None) -> dict:
-    """The paper's promoter Notch model (Table I rates in lattice units) on a
-    64x64 tissue of 16x16-voxel cells, dt = 0.1 s, after 2 s of burn-in:
-    the same timing as the main line (device-resident state, L2 flushed
-    between timed steps, CUDA events on the tissue's stream).  With `run`
-    (the mixed-fidelity tissue) the same for that workload."""
-    import torch
-
-    from paper_1806_10889_gb300.tissue import Tissue
-    from paper_1806_10889_gb300.workloads import fidelity_mask
-
-    run = run or W.promoter()
-    g = Tissue(run.tissue)
-    g.step(run.dt, 20)
-    g.step(run.dt, 3)
-    g.sync()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
-    stream = torch.cuda.current_stream()
-    ev0 = g.total_events()
-    total_ms = chi_ms = 0.0
     for _ in range(args.steps):
-        flush.zero_()
+        flush.zero_()  # L2 flush between timed steps (outside the event pair)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        c_ms, _ = g.step_timed(run.dt, 1)
+        c_ms, s_ms = g.step_timed(args.dt, 1)
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        chi_ms += c_ms
+        sig_ms += s_ms
+    ev1 = g.total_events()
+    after = (g.read_counts(), *g.read_stats()) if check else None
+    events = int((ev1 - ev0).sum())
+    chi_events = int(ev1[0] - ev0[0])
+    total_ms = float(sum(step_ms))
+
+    host = torch.empty(spec.state_ints, dtype=torch.int32, pin_memory=True)
+    g.read_counts_into(host)
+    e0 = g.total_events()
+    k0 = g.get_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        g.write_counts_from(host, step_index=k0 + i)   # H2D of the step's input state
+        g.step(args.dt, 1)
+        g.read_counts_into(host)                       # D2H of the step's result
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e_ev = float((g.total_events() - e0).sum())
+    nbytes = spec.state_ints * 4
+    g.close()
+
+    key = chi_kernel_key(spec.V, launch[1], launch[4]) if launch[0] == 1 else "warp"
+    out = {"metric": MEDIUM_METRIC, "value": events / (total_ms / 1e3), "unit": UNIT,
+           "workload": f"tissue {spec.width}x{spec.height} cells of {spec.n}x{spec.n} voxels, "
+                       f"Notch-Delta model, dt {args.dt}, burn-in {args.burn_in} time units, "
+                       "L2 flushed between timed steps (256 MB write)",
+           "steps": args.steps, "timed_steps_from": base_step,
+           "ms_per_step": total_ms / args.steps,
+           "cell_steps_per_s": spec.cells * args.steps / (total_ms / 1e3),
+           "events_per_step": events / args.steps, "chi_events_per_step": chi_events / args.steps,
+           "chi_ms_per_step": chi_ms / args.steps, "sig_ms_per_step": sig_ms / args.steps,
+           "step_ms_median": statistics.median(step_ms), "step_ms_max": max(step_ms),
+           "chi_launch": {"kernel": ["warp", "persistent"][launch[0]],
+                          "lanes_per_cell": launch[1], "warps_per_block": launch[2],
+                          "smem_layout": ["prefix", "recompute"][launch[4]]},
+           "e2e": {"value": e_ev / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                   "d2h_bytes_per_step": nbytes},
+           "roofline": issue_roofline("medium", chi_events, chi_ms, key, spec.V, spec.cells,
+                                      args.steps, args.steps)}
+    if check:
+        chk = oracle_check([(spec, base_state, base_step, *after)], args.steps, args.dt)
+        out["parity_checked"] = chk["parity_checked"]
+        out["cpu_baseline"] = {"value": chk["events"] / chk["seconds"], "unit": UNIT,
+                               "cores": chk["cores"], "kind": "oracle",
+                               "sample": f"the whole tissue, the {args.steps} timed steps "
+                                         f"{base_step}-{base_step + args.steps - 1} from the GPU's "
+                                         f"state, {chk['events']} events in "
+                                         f"{chk['seconds']:.2f} s",
+                               "single_core": oracle_single_core(spec, base_state, base_step,
+                                                                 args.dt, cells=256)}
+    return out
+
+
+def _timed_tissue(spec, dt: float, burn: int, steps: int, flush: bool = True) -> dict:
+    """Device-timed steps of one tissue after `burn` untimed ones."""
+    import torch
+
+    from paper_1806_10889_gb300.tissue import Tissue
+
+    g = Tissue(spec)
+    if burn:
+        g.step(dt, burn)
+    g.step(dt, 3)
+    g.sync()
+    buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda") if flush else None
+    stream = torch.cuda.current_stream()
+    ev0 = g.total_events()
+    k0 = g.get_step()
+    total_ms = chi_ms = 0.0
+    for _ in range(steps):
+        if buf is not None:
+            buf.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c_ms, _ = g.step_timed(dt, 1)
         b.record(stream)
         b.synchronize()
         total_ms += a.elapsed_time(b)
@@ -341,187 +640,123 @@ def promoter_leg(args, run=None) -> dict:
     ev = g.total_events() - ev0
     launch = g.launch_config()
     g.close()
+    return {"events_per_s": float(ev.sum()) / (total_ms / 1e3),
+            "chi_events_per_s": float(ev[0]) / (chi_ms / 1e3),
+            "cell_steps_per_s": spec.cells * steps / (total_ms / 1e3),
+            "events_per_step": float(ev.sum()) / steps,
+            "face_events_per_step": float(ev[1] + ev[2]) / steps,
+            "ms_per_step": total_ms / steps, "chi_ms_per_step": chi_ms / steps,
+            "steps": steps, "timed_steps_from": k0, "chi_ev": float(ev[0]), "chi_ms": chi_ms,
+            "chi_launch": {"kernel": ["warp", "persistent"][launch[0]],
+                           "lanes_per_cell": launch[1], "warps_per_block": launch[2],
+                           "smem_layout": launch[4]}}
+
+
+def promoter_leg(args, run=None) -> dict:
+    """The paper's promoter Notch model (Table I rates in lattice units) on a
+    64x64 tissue of 16x16-voxel cells, dt = 0.1 s, after 2 s of burn-in.  With
+    `run` (the mixed-fidelity tissue) the same for that workload."""
+    from paper_1806_10889_gb300.workloads import fidelity_mask
+
+    run = run or W.promoter()
     spec = run.tissue
+    r = _timed_tissue(spec, run.dt, 20, args.steps)
     mask = fidelity_mask(spec)
     wm = int(mask.sum()) if mask is not None else 0
-    return {"workload": f"promoter model, {spec.width}x{spec.height} cells of {spec.n}x{spec.n} "
-                        f"voxels, dt 0.1 s, burn-in 2 s, fidelity {spec.fidelity} "
-                        f"({wm} well-mixed cells)",
-            "rates": {k: v for k, v in spec.model.items() if k != "kind"},
-            "events_per_s": float(ev.sum()) / (total_ms / 1e3),
-            "chi_events_per_s": float(ev[0]) / (chi_ms / 1e3),
-            "cell_steps_per_s": spec.cells * args.steps / (total_ms / 1e3),
-            "events_per_step": float(ev.sum()) / args.steps,
-            "face_events_per_step": float(ev[1] + ev[2]) / args.steps,
-            "ms_per_step": total_ms / args.steps, "chi_ms_per_step": chi_ms / args.steps,
-            "chi_launch": {"kernel": ["warp", "persistent"][launch[0]],
-                           "lanes_per_cell": launch[1], "warps_per_block": launch[2]}}
+    r.pop("chi_ev")
+    r.pop("chi_ms")
+    r.update({"workload": f"promoter model, {spec.width}x{spec.height} cells of {spec.n}x{spec.n} "
+                          f"voxels, dt 0.1 s, burn-in 2 s, fidelity {spec.fidelity} "
+                          f"({wm} well-mixed cells)",
+              "rates": {k: v for k, v in spec.model.items() if k != "kind"}})
+    return r
 
 
-def batch_leg(args) -> dict:
-    """The uneven 256-tissue batch: one persistent launch per cell-size class
-    and step (graph-captured, autotuned) against the plain per-tissue launch
-    (every tissue stepped by its own tissue_step call).  Both legs start from
-    the same state and must end bit-identical."""
-    import torch
+def large_leg(args) -> dict:
+    """The large tissue (256x256 cells of 32x32 voxels, 0.8 GB of state, larger
+    than L2) from a burned-in state, with its chi roofline."""
+    lg = W.large()
+    burn = int(round(args.large_burn_in / lg.dt))
+    r = _timed_tissue(lg.tissue, lg.dt, burn, args.large_steps, flush=False)
+    cl = r["chi_launch"]
+    key = chi_kernel_key(lg.tissue.V, cl["lanes_per_cell"], cl["smem_layout"])
+    r["roofline"] = issue_roofline("large", r.pop("chi_ev"), r.pop("chi_ms"), key, lg.tissue.V,
+                                   lg.tissue.cells, args.large_steps, args.large_steps)
+    r["workload"] = (f"tissue 256x256 cells of 32x32 voxels, Notch-Delta model, dt 0.1, "
+                     f"burn-in {args.large_burn_in} time units; state larger than L2, no flush")
+    return r
 
-    from paper_1806_10889_gb300 import autotune
-    from paper_1806_10889_gb300.batching import Batch
-    from paper_1806_10889_gb300.tissue import Tissue
 
-    runs = W.batch()
-    dt, K = runs[0].dt, args.batch_steps
-    cells = sum(r.tissue.cells for r in runs)
-    plain = [Tissue(r.tissue) for r in runs]
-    for t in plain:
-        t.step(dt, 1)
-    torch.cuda.synchronize()
-    ev0 = sum(int(t.total_events().sum()) for t in plain)
-    stream = torch.cuda.current_stream()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(K):
-        for t in plain:
-            t.step(dt, 1)
-    b.record(stream)
-    b.synchronize()
-    plain_ms = a.elapsed_time(b)
-    plain_events = sum(int(t.total_events().sum()) for t in plain) - ev0
+# ---------------------------------------------------------------------------
+# Serving
+# ---------------------------------------------------------------------------
 
-    members = [Tissue(r.tissue) for r in runs]
-    torch.cuda.synchronize()
-    bt = Batch(members)
-    bt.step(dt, 1)
-    bt.sync()
-    tuned = autotune.tune_batch(members, dt, steps=1, max_clones=24) if args.autotune else None
-    if tuned:
-        autotune.apply_batch(bt, tuned)
-    ev1 = sum(int(m.total_events().sum()) for m in members)
-    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a2.record(bt.stream)
-    bt.step(dt, K)
-    b2.record(bt.stream)
-    b2.synchronize()
-    batch_ms = a2.elapsed_time(b2)
-    bt.sync()
-    batch_events = sum(int(m.total_events().sum()) for m in members) - ev1
-    same = all(np.array_equal(x.read_counts(), y.read_counts()) for x, y in zip(plain, members))
-    bt.close()
-    for t in plain + members:
-        t.close()
-    return {"workload": "256 uneven tissues (side 2..64, n in {8,16,32}, kD U[5,20]), dt 0.1",
-            "cells": cells, "steps": K,
-            "batched_events_per_s": batch_events / (batch_ms / 1e3),
-            "plain_events_per_s": plain_events / (plain_ms / 1e3),
-            "speedup": (batch_events / batch_ms) / (plain_events / plain_ms),
-            "batched_cell_steps_per_s": cells * K / (batch_ms / 1e3),
-            "batched_ms_per_step": batch_ms / K, "plain_ms_per_step": plain_ms / K,
-            "bit_identical": bool(same),
-            "tuned": None if not tuned else {
-                "classes": {str(k): list(v) for k, v in tuned["classes"].items()},
-                "steps_per_graph": tuned["steps_per_graph"]}}
+def serving_requests(count: int, max_replicas: int):
+    """The first `count` requests of the serving workload with at most
+    `max_replicas` replicas each (the request mix, sides and seeds unchanged)."""
+    return [replace(q, replicas=min(q.replicas, max_replicas)) for q in W.serving()[:count]]
 
 
 def serving_leg(args) -> dict:
-    """The first --serving requests of the serving workload (Poisson arrivals
-    at 50 req/s, 1..64 replicas, lognormal sides, 16x16 voxels, T = 20),
-    admitted by a device-memory budget and served by continuous batching;
-    against the plain alternative of serving them one tissue at a time."""
+    """Continuous-batching server on `--serving` requests of the serving
+    workload (replicas capped at --serving-replicas so that one GB300 can keep
+    up): saturation throughput with every request arriving at the workload's
+    50 req/s, then p50/p99 latency with the arrival gaps stretched to a
+    sustainable rate (a fraction of the measured saturation rate), and the
+    plain one-tissue-at-a-time rate on the first few requests."""
     import torch
 
     from paper_1806_10889_gb300.serving import Server, latency_summary
     from paper_1806_10889_gb300.tissue import Tissue
 
-    reqs = W.serving()[: args.serving]
+    reqs = serving_requests(args.serving, args.serving_replicas)
     free, _ = torch.cuda.mem_get_info()
-    srv = Server(budget_bytes=int(free * 0.6), chunk_steps=10)
+    budget = int(free * 0.6)
+    srv = Server(budget_bytes=budget, chunk_steps=10)
     t0 = time.perf_counter()
     res = srv.run(reqs)
     wall = time.perf_counter() - t0
-    out = {"requests": len(reqs), "arrivals_per_s": 50.0, "budget_bytes": srv.budget,
+    sat = {"arrivals_per_s": 50.0, "wall_s": wall, "served_events_per_s": srv.device_events / wall,
+           "requests_per_s": len(reqs) / wall, "latency": latency_summary(res),
+           "rebuilds": srv.rebuilds, "rebuild_s": srv.rebuild_s}
+    out = {"requests": len(reqs), "max_replicas": args.serving_replicas, "budget_bytes": budget,
            "policy": f"{srv.policy} (rounds of at least {srv.fill_cells} cells)",
-           "served_events_per_s": srv.device_events / wall, "wall_s": wall,
-           "latency": latency_summary(res)}
+           "saturation": sat}
+    # a sustainable rate: arrivals at args.serving_load x the saturation rate
+    rate = args.serving_load * sat["requests_per_s"]
+    scale = 50.0 / rate
+    srv2 = Server(budget_bytes=budget, chunk_steps=10)
+    t0 = time.perf_counter()
+    res2 = srv2.run(reqs, time_scale=scale)
+    wall2 = time.perf_counter() - t0
+    out["sustained"] = {"arrivals_per_s": rate, "time_scale": scale, "wall_s": wall2,
+                        "served_events_per_s": srv2.device_events / wall2,
+                        "latency": latency_summary(res2), "rebuilds": srv2.rebuilds,
+                        "rebuild_s": srv2.rebuild_s}
+    out["same_results"] = all(a.digest == b.digest for a, b in zip(res, res2))
     if args.serving_plain:
+        sub = reqs[: args.serving_plain]
         ev, t1 = 0, time.perf_counter()
-        for q in reqs:
+        for q in sub:
             for spec in q.replica_specs():
                 t = Tissue(spec)
                 t.step(q.dt, q.n_steps)
                 ev += int(t.total_events().sum())
                 t.close()
         torch.cuda.synchronize()
-        out["plain_events_per_s"] = ev / (time.perf_counter() - t1)
-        out["served_vs_plain"] = out["served_events_per_s"] / out["plain_events_per_s"]
+        el = time.perf_counter() - t1
+        sub_ev = sum(r.events for r in res[: args.serving_plain])
+        out["plain"] = {"requests": len(sub), "plain_events_per_s": ev / el,
+                        "note": "the first requests served one tissue at a time, in arrival "
+                                "order, with no batching",
+                        "events_match": ev == sub_ev}
+        out["served_vs_plain"] = sat["served_events_per_s"] / (ev / el)
     return out
 
 
-def _oracle_patch(side: int):
-    import oracle as O
-    spec = W.medium(0.1).tissue
-    d = O.Desc(side, side, spec.n, seed=spec.seed, tissue_id=spec.tissue_id,
-               init_lambda=tuple(spec.init_lambda))
-    return O, d, O.Model(**spec.model)
-
-
-def cpu_baseline(args, state=None, step0: int = 0, side: int = 64, budget_s: float = 10.0,
-                 max_steps: int = 30):
-    """The oracle, as it stands, on the benchmark tissue: whole-tissue steps
-    from the state the timed GPU steps start from (after the burn-in), until
-    about budget_s seconds of CPU work are done."""
-    O, d, m = _oracle_patch(side)
-    counts = O.init_counts(d) if state is None else np.array(state, dtype=np.int32, copy=True)
-    threads = O.max_threads()
-    total, steps = 0, 0
-    t0 = time.perf_counter()
-    while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < budget_s):
-        ne, _ = O.step(d, m, counts, step0 + steps, 1, args.dt, n_threads=threads)
-        total += int(ne.sum())
-        steps += 1
-    dt_s = time.perf_counter() - t0
-    start = "the state after the GPU burn-in" if state is not None else "the initial state"
-    # one core: chi of the first 256 cells of the same starting state
-    one = O.init_counts(d) if state is None else np.array(state, dtype=np.int32, copy=True)
-    ev1, t1 = 0, time.perf_counter()
-    for c in range(256):
-        ev1 += O.chi_cell(d, m, one, c, step0, args.dt)[0]
-    t1 = time.perf_counter() - t1
-    return {"value": total / dt_s, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{side}x{side} cells of the medium tissue (16x16 voxels), {steps} steps "
-                      f"from {start} (steps {step0}-{step0 + steps - 1}), dt {args.dt}, "
-                      f"{total} events in {dt_s:.2f} s",
-            "single_core": {"value": ev1 / t1, "unit": UNIT, "cores": 1,
-                            "sample": f"chi of cells 0-255 at step {step0}, {ev1} events in "
-                                      f"{t1:.2f} s"}}
-
-
-def run_reference(args, rank, world):
-    if rank != 0:
-        return None
-    O, d, m = _oracle_patch(args.ref_side)
-    counts = O.init_counts(d)
-    threads = O.max_threads()
-    burn = int(round(args.burn_in / args.dt))  # the same untimed burn-in as the GPU arm
-    for k in range(burn + args.warmup):
-        O.step(d, m, counts, k, 1, args.dt, n_threads=threads)
-    total, t0 = 0, time.perf_counter()
-    for k in range(burn + args.warmup, burn + args.warmup + args.steps):
-        ne, _ = O.step(d, m, counts, k, 1, args.dt, n_threads=threads)
-        total += int(ne.sum())
-    el = time.perf_counter() - t0
-    value = total / el
-    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
-            "impl": "reference",
-            "config": {"workload": "medium tissue 64x64 cells of 16x16 voxels, Notch-Delta model",
-                       "dt": args.dt, "burn_in_time": args.burn_in,
-                       "sample_cells": args.ref_side ** 2},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{args.ref_side}x{args.ref_side}-cell patch of the medium "
-                                       f"tissue per step, after {burn} burn-in steps"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-
+# ---------------------------------------------------------------------------
+# Suite: every configuration, GPU and oracle, for the results table
+# ---------------------------------------------------------------------------
 
 def _gpu_rate(spec, dt, steps, burn=0, config=None):
     """Device-timed rate of `steps` splitting steps after `burn` untimed ones:
@@ -613,9 +848,207 @@ def run_suite(args) -> dict:
     for dt, burn, steps in ((0.01, 2000, 50), (0.1, 200, 10), (1.0, 20, 3)):
         row(f"medium_dt{dt}", W.medium(dt).tissue, dt, steps, burn, cpu_steps=2 if dt < 1 else 1)
     lg = W.large()
-    row("large", lg.tissue, lg.dt, 2, 0, cpu_steps=0, cpu_cells=128)
-    out["large"]["cpu_sample"] = "chi of 128 cells at step 0 (one core); all cores not run"
+    burn = int(round(args.large_burn_in / lg.dt))
+    row("large", lg.tissue, lg.dt, max(args.large_steps, 1), burn, cpu_steps=0, cpu_cells=128)
+    out["large"]["cpu_sample"] = (f"chi of 128 cells at step {burn} (one core); all cores "
+                                  "not run")
     return out
+
+
+
+# ---------------------------------------------------------------------------
+# Profiling case for the instructions-per-event table
+# ---------------------------------------------------------------------------
+
+def profile_subset(runs, per_class: int = 16, target_cells: int = 1024):
+    """A smaller batch with every cell-size class of the full one: per cell
+    size the `per_class` member tissues nearest target_cells cells (about
+    260 MB of state, more than L2, so DRAM figures stay meaningful)."""
+    return oracle_sample(runs, per_class=per_class, target_cells=target_cells)
+
+
+def run_profile(args) -> dict:
+    """Steps one workload as the benchmark does (burn-in, warm-up, then
+    --steps steps) and reports each class's chi launch key and chi events
+    per step, so that ncu's per-launch counters of the same run give
+    instructions and DRAM bytes per event.  Workloads: "batch" (a subset of
+    the batch with every cell-size class), "medium" and "large".  Under ncu,
+    skip the chi launches of the burn-in and warm-up (launches_before in the
+    output) and capture launches_per_step x steps of them."""
+    import torch
+
+    from paper_1806_10889_gb300.batching import Batch
+    from paper_1806_10889_gb300.tissue import Tissue
+
+    if args.profile_chi == "batch":
+        runs = batch_runs()
+        idx = profile_subset(runs)
+        sub = [runs[i] for i in idx]
+        burn_time = args.batch_burn_in
+    else:
+        run = W.medium(args.dt) if args.profile_chi == "medium" else W.large()
+        idx, sub = [0], [run]
+        burn_time = args.burn_in if args.profile_chi == "medium" else args.large_burn_in
+    dt = sub[0].dt
+    members = [Tissue(r.tissue) for r in sub]
+    torch.cuda.synchronize()
+    if args.profile_chi == "batch":
+        bt = Batch(members)
+        classes = bt.classes()
+        step = bt.step
+
+        def sync():
+            bt.sync()
+    else:
+        g = members[0]
+        la = g.launch_config()
+        classes = [{"V": g.spec.V, "lanes_per_cell": la[1], "warps_per_block": la[2],
+                    "smem_layout": la[4], "cells": g.spec.cells}]
+        step, sync = g.step, g.sync
+    keys = [chi_kernel_key(c["V"], c["lanes_per_cell"], c["smem_layout"]) for c in classes]
+    per_step = sum(1 + int(k.endswith("u16")) for k in keys)
+    burn = int(round(burn_time / dt))
+    step(dt, burn + args.warmup)
+    sync()
+    steps = []
+    for _ in range(args.steps):
+        e0 = _events(members)
+        step(dt, 1)
+        sync()
+        d = _events(members) - e0
+        steps.append([int(sum(d[j, 0] for j, r in enumerate(sub) if r.tissue.V == c["V"]))
+                      for c in classes])
+    if args.profile_chi == "batch":
+        bt.close()
+    for m in members:
+        m.close()
+    return {"workload": args.profile_chi, "tissues": idx,
+            "cells": sum(r.tissue.cells for r in sub),
+            "state_bytes": sum(r.tissue.state_ints * 4 for r in sub),
+            "classes": [dict(c, key=k) for c, k in zip(classes, keys)],
+            "chi_launches_per_step": per_step,
+            "launches_before": per_step * (burn + args.warmup),
+            "chi_events_per_step_by_class": steps, "sources": chi_sources_sha()}
+
+
+# ---------------------------------------------------------------------------
+# Bound on a wavefront across steps
+# ---------------------------------------------------------------------------
+
+def wavefront_bound(events: np.ndarray, width: int, height: int) -> dict:
+    """How much a barrier-free wavefront across steps could shorten K steps of
+    one tissue, in events along the longest chain (a cell's chi events are one
+    dependent chain, so its time is proportional to them).
+
+    events[k, c]: chi events of cell c in step k.  With a barrier per step,
+    K steps take sum_k max_c e[k, c].  Without one, cell c may start step k
+    once the faces it touches are done for step k-1; the two face phases make
+    that the 3x3 neighbourhood of c, so the finish of (c, k) is
+    F[c, k] = max over that neighbourhood of F[., k-1] + e[k, c], and the
+    wavefront takes max_c F[c, K-1].  Both ignore the (short) face phases."""
+    e = np.asarray(events, dtype=np.float64).reshape(-1, height, width)
+    barrier = float(e.max(axis=(1, 2)).sum())
+    chain = float(e.sum(axis=0).max())
+    F = np.zeros((height, width))
+    for k in range(e.shape[0]):
+        p = np.pad(F, 1)
+        nb = np.max(np.stack([p[1 + dy:1 + dy + height, 1 + dx:1 + dx + width]
+                              for dy in (-1, 0, 1) for dx in (-1, 0, 1)]), axis=0)
+        F = nb + e[k]
+    wave = float(F.max())
+    return {"steps": int(e.shape[0]), "barrier_events": barrier, "wavefront_events": wave,
+            "slowest_cell_events": chain, "gain_bound": 1.0 - wave / barrier,
+            "mean_over_max_per_step": float((e.mean(axis=(1, 2)) / e.max(axis=(1, 2))).mean())}
+
+
+def run_wavefront(args) -> dict:
+    """The medium tissue after its burn-in, --steps steps with every cell's
+    chi events read back after each step, and the bound above."""
+    from paper_1806_10889_gb300.tissue import Tissue
+
+    spec = W.medium(args.dt).tissue
+    g = Tissue(spec)
+    g.step(args.dt, int(round(args.burn_in / args.dt)))
+    ev = []
+    for _ in range(args.steps):
+        g.step(args.dt, 1)
+        ev.append(g.read_stats()[0][0].astype(np.int64))
+    g.close()
+    out = wavefront_bound(np.array(ev), spec.width, spec.height)
+    out["workload"] = (f"medium tissue {spec.width}x{spec.height} cells of {spec.n}x{spec.n} "
+                       f"voxels, dt {args.dt}, after {args.burn_in} time units")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Driver
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    out = batch_headline(args, rank, world, dist)
+    if rank == 0 and world == 1:
+        if not args.no_medium:
+            out["medium"] = medium_leg(args)
+        if not args.no_promoter:
+            out["promoter"] = promoter_leg(args)
+            out["mixed_fidelity"] = promoter_leg(args, W.mixed_fidelity())
+        if args.large_steps:
+            out["large"] = large_leg(args)
+        if args.serving:
+            out["serving"] = serving_leg(args)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores: each step is the same
+    splitting step of the sampled member tissues of the batch (one per cell
+    size), after the same simulated burn-in as the GPU arm."""
+    if rank != 0:
+        return None
+    import oracle as O
+    runs = W.batch()
+    dt = runs[0].dt
+    sample = oracle_sample(runs, per_class=args.oracle_per_class)
+    tissues = []
+    for i in sample:
+        _, d, m = _orc(runs[i].tissue)
+        tissues.append((d, m, O.init_counts(d)))
+    threads = O.max_threads()
+    burn = int(round(args.batch_burn_in / dt))
+    for k in range(burn + args.warmup):
+        for d, m, c in tissues:
+            O.step(d, m, c, k, 1, dt, n_threads=threads)
+    total, t0 = 0, time.perf_counter()
+    for k in range(burn + args.warmup, burn + args.warmup + args.steps):
+        for d, m, c in tissues:
+            ne, _ = O.step(d, m, c, k, 1, dt, n_threads=threads)
+            total += int(ne.sum())
+    el = time.perf_counter() - t0
+    value = total / el
+    cells = sum(runs[i].tissue.cells for i in sample)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "256 uneven tissues (side U{2..64} cells, cells of 8x8, 16x16 "
+                                   "or 32x32 voxels, kD U[5,20]), Notch-Delta model; the oracle "
+                                   "steps a sample of them",
+                       "dt": dt, "burn_in_time": args.batch_burn_in, "sample_tissues": sample,
+                       "sample_cells": cells},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"member tissues {sample} of the batch ({cells} cells), "
+                                       f"whole splitting steps after {burn} burn-in steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
@@ -624,33 +1057,48 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--dt", type=float, default=0.1, choices=[0.01, 0.1, 1.0])
-    ap.add_argument("--burn-in", type=float, default=20.0, help="untimed simulated time first")
+    ap.add_argument("--batch-burn-in", type=float, default=5.0,
+                    help="untimed simulated time of the batch before its timed steps")
+    ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--tune-clones", type=int, default=8,
+                    help="member tissues per cell-size class the autotuner clones")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--plain-steps", type=int, default=2,
+                    help="steps of the plain per-tissue comparison (0: skip)")
+    ap.add_argument("--oracle-per-class", type=int, default=1)
+    ap.add_argument("--dt", type=float, default=0.1, choices=[0.01, 0.1, 1.0],
+                    help="medium tissue: splitting step")
+    ap.add_argument("--burn-in", type=float, default=20.0,
+                    help="medium tissue: untimed simulated time first")
     ap.add_argument("--chi-wpb", type=int, default=0)
-    ap.add_argument("--kernel", choices=["default", "warp", "persistent"], default="default")
+    ap.add_argument("--kernel", choices=["default", "persistent"], default="default")
     ap.add_argument("--lanes", type=int, choices=[8, 16, 32], default=16)
     ap.add_argument("--layout", type=int, choices=[0, 1], default=0,
                     help="persistent kernel: 0 prefix arrays, 1 recompute")
-    ap.add_argument("--chi-traffic", type=float, default=None,
-                    help="DRAM bytes per chi launch from an ncu capture, if known")
-    ap.add_argument("--ref-side", type=int, default=16)
-    ap.add_argument("--side", type=int, default=0, help="profiling only: tissue side in cells")
+    ap.add_argument("--side", type=int, default=0, help="profiling only: medium tissue side")
     ap.add_argument("--n", type=int, default=0, help="profiling only: voxels per cell side")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain leg")
-    ap.add_argument("--batch-steps", type=int, default=3)
-    ap.add_argument("--autotune", type=int, default=1)
-    ap.add_argument("--workload", choices=["medium", "promoter", "mixed"], default="medium",
-                    help="main line: the medium Notch-Delta tissue (the benchmark), or the "
-                         "promoter or mixed-fidelity tissue (profiling)")
+    ap.add_argument("--no-medium", action="store_true")
     ap.add_argument("--no-promoter", action="store_true",
                     help="skip the promoter-model and mixed-fidelity legs")
-    ap.add_argument("--serving", type=int, default=4,
+    ap.add_argument("--large-steps", type=int, default=3, help="large tissue timed steps (0: skip)")
+    ap.add_argument("--large-burn-in", type=float, default=2.0)
+    ap.add_argument("--serving", type=int, default=50,
                     help="serve the first K requests of the serving workload (0: skip)")
-    ap.add_argument("--serving-plain", action="store_true")
+    ap.add_argument("--serving-replicas", type=int, default=2,
+                    help="cap on the replicas of each served request")
+    ap.add_argument("--serving-load", type=float, default=0.7,
+                    help="sustained arrival rate as a fraction of the saturation rate")
+    ap.add_argument("--serving-plain", type=int, default=4,
+                    help="requests served one tissue at a time for the plain rate (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-chi", choices=["batch", "medium", "large"], default=None,
+                    help="profiling case: step this workload, printing each chi launch class's "
+                         "events per step for ncu's per-launch counters")
+    ap.add_argument("--wavefront", action="store_true",
+                    help="bound the gain of a barrier-free wavefront across --steps steps of "
+                         "the medium tissue (per-cell events read back every step)")
     ap.add_argument("--suite", action="store_true",
-                    help="measure every configuration of the suite (GPU and oracle) and print "
+                    help="measure every single-tissue configuration (GPU and oracle) and print "
                          "one JSON object instead of the benchmark line (several minutes)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -658,6 +1106,12 @@ def main():
     rank, world, local_rank = _env_rank()
     if args.suite:
         print(json.dumps(run_suite(args)))
+        return
+    if args.profile_chi:
+        print(json.dumps(run_profile(args)))
+        return
+    if args.wavefront:
+        print(json.dumps(run_wavefront(args)))
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)

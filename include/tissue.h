@@ -270,6 +270,28 @@ int tissue_batch_sync(tissue_batch* b);
 int tissue_batch_info(const tissue_batch* b, uint32_t* n_members, uint32_t* n_classes,
                       uint64_t* n_cells);
 
+/* Cell-size class i (0 <= i < n_classes of tissue_batch_info; largest cells
+ * first): its cell size V, the launch shape of its chi launch and its number
+ * of lattice cells (any pointer may be NULL). */
+int tissue_batch_class_info(const tissue_batch* b, uint32_t i, uint32_t* V,
+                            uint32_t* lanes_per_cell, uint32_t* warps_per_block,
+                            uint32_t* smem_layout, uint32_t* cells);
+
+/* Diagnostic timing of batch steps (a measurement aid; the paper has no
+ * counterpart).  With on = 1 every following step records CUDA events on the
+ * batch stream around each class's chi launches and around the whole step;
+ * a captured step holds them as event-record nodes of its graph.  Results
+ * never depend on it.  Toggling it drops the captured graph. */
+int tissue_batch_set_timing(tissue_batch* b, uint32_t on);
+
+/* Device milliseconds of the last step enqueued with timing on: the whole
+ * step, the well-mixed chi launch (0 when the batch has no well-mixed cell)
+ * and the chi launches of each class i < n (the 16-bit-count launch and its
+ * 32-bit redo pass together).  Waits for the batch stream.  TISSUE_E_ARG if
+ * timing is off or no timed step has run. */
+int tissue_batch_read_timing(tissue_batch* b, double* step_ms, double* wm_ms, double* class_ms,
+                             uint32_t n);
+
 void tissue_batch_destroy(tissue_batch* b);
 
 /* Largest tissue (width*height cells) tissue_step_noalloc accepts. */

@@ -91,9 +91,13 @@ def _time_steps(run, n_steps: int, stream=None) -> float:
 
 def tune_tissue(spec: TissueSpec, dt: float, state: np.ndarray | None = None,
                 step_index: int = 0, steps: int = 2, candidates: list[tuple] | None = None,
-                use_cache: bool = True) -> dict:
+                use_cache: bool = True, on_candidate=None) -> dict:
     """Pick the fastest chi launch for this tissue; returns
-    {"config": (kernel, lanes, warps, blocks, layout), "ms": {str(config): ms}}."""
+    {"config": (kernel, lanes, warps, blocks, layout), "ms": {str(config): ms}}.
+
+    on_candidate(config, tissue), if given, runs after each candidate's clone
+    is set up and before it steps (a hook for tests of the bit-identity
+    check)."""
     key = f"tissue|{_gpu_name()}|V={spec.V}|cells~{_size_class(spec.cells)}|dt={dt}"
     if use_cache and candidates is None:
         hit = _load().get(key)
@@ -111,6 +115,8 @@ def tune_tissue(spec: TissueSpec, dt: float, state: np.ndarray | None = None,
             t.close()
             continue
         tried.append(cfg)
+        if on_candidate is not None:
+            on_candidate(cfg, t)
         t.step(dt, 1)  # warm (first launch of a variant configures it)
         t.sync()
         times[str(cfg)] = _time_steps(lambda n: t.step(dt, n), steps)
@@ -129,13 +135,16 @@ def tune_tissue(spec: TissueSpec, dt: float, state: np.ndarray | None = None,
 
 
 def tune_batch(members: list[Tissue], dt: float, steps: int = 1, max_clones: int = 48,
-               schedules=(1, 4), use_cache: bool = True) -> dict:
+               schedules=(1, 4), use_cache: bool = True, on_candidate=None) -> dict:
     """Pick (lanes per cell, warps per block, layout) per cell-size class and the
     steps-per-graph schedule for a batch of these tissues.
 
     Each class is tuned on clones of up to ``max_clones`` of its members
     (their current state and step index), so the members themselves do not
     move.  Returns {"classes": {V: (lanes, warps, layout)}, "steps_per_graph": k}.
+    on_candidate((V, lanes, warps, layout), clones), if given, runs after each
+    class candidate's clones are set up and before they step (a hook for
+    tests of the bit-identity check).
     """
     from .batching import Batch
 
@@ -173,6 +182,8 @@ def tune_batch(members: list[Tissue], dt: float, steps: int = 1, max_clones: int
                     c.close()
                 continue
             tried.append((lanes, wpb, layout))
+            if on_candidate is not None:
+                on_candidate((V, lanes, wpb, layout), clones)
             b.step(dt, 1)
             b.sync()
             ms_ = _time_steps(lambda n: b.step(dt, n), steps, b.stream)

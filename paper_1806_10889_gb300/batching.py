@@ -52,6 +52,32 @@ class Batch:
                "tissue_batch_info")
         return int(a.value), int(b.value), int(c.value)
 
+    def classes(self) -> list[dict]:
+        """Cell-size classes, largest cells first: V, launch shape, cells."""
+        n = self.info()[1]
+        out = []
+        for i in range(n):
+            v = [C.c_uint32() for _ in range(5)]
+            _check(lib().tissue_batch_class_info(self._h, i, *[C.byref(x) for x in v]),
+                   "tissue_batch_class_info")
+            V, lanes, wpb, layout, cells = (int(x.value) for x in v)
+            out.append({"V": V, "lanes_per_cell": lanes, "warps_per_block": wpb,
+                        "smem_layout": layout, "cells": cells})
+        return out
+
+    def set_timing(self, on: bool) -> None:
+        """Record device times of each following step (a measurement aid)."""
+        _check(lib().tissue_batch_set_timing(self._h, 1 if on else 0), "tissue_batch_set_timing")
+
+    def read_timing(self):
+        """(step ms, well-mixed chi ms, [chi ms per class]) of the last timed step."""
+        n = self.info()[1]
+        st, wm = C.c_double(), C.c_double()
+        cls = (C.c_double * max(n, 1))()
+        _check(lib().tissue_batch_read_timing(self._h, C.byref(st), C.byref(wm), cls, n),
+               "tissue_batch_read_timing")
+        return st.value, wm.value, [cls[i] for i in range(n)]
+
     def total_events(self) -> int:
         return int(sum(int(m.total_events().sum()) for m in self.members))
 

@@ -56,10 +56,11 @@ struct Seg {
   int centre;       // the promoter voxel (n/2, n/2)
 };
 
-// The model terms c0, c1 and X of a voxel (see the file comment).
+// The model terms c0, c1 and X of a voxel (see the file comment); hR is the
+// Hill production Hill(R) of the Notch-Delta model (unused by the promoter).
 template <bool GEN>
 __device__ __forceinline__ void voxel_terms(bool pm, const QRates& q, int v, const Seg& s,
-                                            uint32_t D, uint32_t N, uint32_t R, bool act,
+                                            uint32_t D, uint32_t N, uint32_t R, uint64_t hR,
                                             uint64_t& c0, uint64_t& c1, uint64_t& X) {
   if (GEN && pm) {
     const uint32_t F = static_cast<uint32_t>(v == s.centre) - R;
@@ -67,11 +68,48 @@ __device__ __forceinline__ void voxel_terms(bool pm, const QRates& q, int v, con
     c1 = q.kd * R;
     X = static_cast<uint64_t>(N) * F;
   } else {
-    c0 = act ? hill_q(q, R) : 0ull;  // no table read for an idle segment
+    c0 = hR;
     c1 = q.kN;
     X = static_cast<uint64_t>(D) * N;
   }
 }
+
+// Hill values held in registers: with one cell per warp (H = 32), lane j
+// keeps Hill(j), read from its tissue's table when the warp takes a cell.
+// Repressor counts per voxel are small (a few tens in a running tissue), so
+// most lookups of the event loop become register shuffles instead of table
+// loads on the event's dependency chain; larger counts fall back to the
+// table.  With 16 or 8 lanes the two extra registers cost more than they
+// save (a resident block per SM at 16 lanes; same-box A/B), so those
+// instantiations read the table (kSets = 0).  The code handles up to two
+// sets per lane (Hill(j) and Hill(j + H)).
+template <int H>
+struct HillRegs {
+  static constexpr int kSets = H == 32 ? 1 : 0;
+  static constexpr uint32_t kCover = static_cast<uint32_t>(kSets * H);
+  uint64_t h0 = 0, h1 = 0;
+
+  __device__ __forceinline__ void load(const QRates& q, int sl) {
+    if (kSets >= 1) h0 = __ldg(q.hill + sl);
+    if (kSets >= 2) h1 = __ldg(q.hill + sl + H);
+  }
+
+  // Hill(R) for this lane's R; every lane of the warp must call it (the
+  // shuffles are warp-wide).  `act` gates the table fallback so an idle
+  // segment reads nothing.
+  __device__ __forceinline__ uint64_t get(const QRates& q, uint32_t R, bool act) const {
+    uint64_t x = 0ull;
+    if (kSets >= 1) {
+      const int src = static_cast<int>(R & static_cast<uint32_t>(H - 1));
+      x = __shfl_sync(kFull, h0, src, H);
+      if (kSets >= 2) {
+        const uint64_t y = __shfl_sync(kFull, h1, src, H);
+        x = (R & static_cast<uint32_t>(H)) ? y : x;
+      }
+    }
+    return R < kCover ? x : (act ? hill_q(q, R) : 0ull);
+  }
+};
 
 // Existence mask of the four neighbour directions (-x, +x, -y, +y) of v.
 __device__ __forceinline__ uint32_t dir_mask(int v, const Seg& s) {
@@ -80,18 +118,15 @@ __device__ __forceinline__ uint32_t dir_mask(int v, const Seg& s) {
          (static_cast<uint32_t>(vy > 0) << 2) | (static_cast<uint32_t>(vy < s.n - 1) << 3);
 }
 
-// Total propensity of voxel v (see voxel_total in k_chi.cu; same value).
-template <bool GEN, typename CT>
-__device__ __forceinline__ uint64_t seg_voxel_total(const CT* cnt, int vmax, int v,
-                                                    const Seg& s, const QRates& q, bool pm,
-                                                    bool& ovf, bool& oob) {
-  const int vi = static_cast<int>(TSG_IDX(v, vmax, oob));
-  const uint32_t D = static_cast<uint32_t>(cnt[vi]);
-  const uint32_t N = static_cast<uint32_t>(cnt[vmax + vi]);
-  const uint32_t R = static_cast<uint32_t>(cnt[2 * vmax + vi]);
+// Total propensity of voxel v (see voxel_total in k_chi.cu; same value),
+// given the voxel's counts and its Hill value hR.
+template <bool GEN>
+__device__ __forceinline__ uint64_t voxel_total_of(int v, uint32_t D, uint32_t N, uint32_t R,
+                                                   uint64_t hR, const Seg& s, const QRates& q,
+                                                   bool pm, bool& ovf) {
   const int nn = __popc(dir_mask(v, s));
   uint64_t c0, c1, X;
-  voxel_terms<GEN>(pm, q, v, s, D, N, R, true, c0, c1, X);
+  voxel_terms<GEN>(pm, q, v, s, D, N, R, hR, c0, c1, X);
   const uint64_t base = c0 + c1;
   if ((D | N | R) < q.small) {
     return base + q.cD[nn] * D + q.cN[nn] * N + q.cRo[nn] * R + q.k_in * X;
@@ -104,6 +139,20 @@ __device__ __forceinline__ uint64_t seg_voxel_total(const CT* cnt, int vmax, int
   a += mul_lim(q.k_off, R, ovf);
   ovf |= (a >> 52) != 0ull;
   return a;
+}
+
+// Total propensity of voxel v from the counts in shared memory, its Hill
+// value read from the table.
+template <bool GEN, typename CT>
+__device__ __forceinline__ uint64_t seg_voxel_total(const CT* cnt, int vmax, int v,
+                                                    const Seg& s, const QRates& q, bool pm,
+                                                    bool& ovf, bool& oob) {
+  const int vi = static_cast<int>(TSG_IDX(v, vmax, oob));
+  const uint32_t D = static_cast<uint32_t>(cnt[vi]);
+  const uint32_t N = static_cast<uint32_t>(cnt[vmax + vi]);
+  const uint32_t R = static_cast<uint32_t>(cnt[2 * vmax + vi]);
+  const uint64_t hR = (GEN && pm) ? 0ull : hill_q(q, R);
+  return voxel_total_of<GEN>(v, D, N, R, hR, s, q, pm, ovf);
 }
 
 // Lane constants for the closed-form running sum C_j of channel j: which of
@@ -163,7 +212,7 @@ __device__ __forceinline__ uint64_t chan_cum(const ChanLane& c, const LaneK& k, 
 // items[0 .. n) are the work (n = *n_items_dev when that is given, else
 // n_items); NARROW appends the cells it gives up on to redo[*redo_n ...].
 template <int H, bool PRE, bool QB, int GEN, bool NARROW>
-__global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
+__global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (NARROW ? 5 : 8)) k_chi_seg(
                                                  const TissueView* __restrict__ views,
                                                  const uint2* __restrict__ items,
                                                  const uint32_t n_items, uint32_t* counter,
@@ -171,7 +220,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
                                                  const uint32_t step_off, const double dt,
                                                  uint2* __restrict__ redo, uint32_t* redo_n,
                                                  const uint32_t* n_items_dev) {
-  static_assert(!NARROW || (PRE && GEN == 0), "16-bit counts: prefix layout, Notch-Delta only");
+  static_assert(!NARROW || GEN == 0, "16-bit counts: Notch-Delta only");
   using CT = typename std::conditional<NARROW, uint16_t, int32_t>::type;
   constexpr int G = 32 / H;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -188,6 +237,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
   const ChanLane cl = chan_lane(sl);
   const ChanLane cl2 = chan_lane(sl + H);  // second channel of each lane when H = 8
   LaneK lk{}, lk2{};                         // their coefficients for the current cell
+  HillRegs<H> hreg;                          // Hill(R) of small R for the current cell
 
   static_assert(PRE || !QB, "the recompute layout needs B <= H");
   bool have = false, done = false, pm = false;
@@ -228,6 +278,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
         pm = GEN == 2 || (GEN == 1 && sv->q.kind == kModelPromoter);
         lk = lane_k(cl, sv->q);
         if (H == 8) lk2 = lane_k(cl2, sv->q);
+        if (GEN != 2) hreg.load(sv->q, sl);
         const bool skip = kChecked && (s.V > vmax || cell >= sv->width * sv->height);
         if (skip) {
           // the cell does not fit this launch's shared memory, or is not in
@@ -370,8 +421,14 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
       // the block's voxel propensities, recomputed, then their running sum
       bool unused = false;
       const bool mine = act && sl < s.B && vb + sl < s.V;
+      const int bx = mine ? vb + sl : 0;
+      const int bi = static_cast<int>(TSG_IDX(bx, vmax, oob));
+      const uint32_t bD = static_cast<uint32_t>(cnt[bi]);
+      const uint32_t bN = static_cast<uint32_t>(cnt[vmax + bi]);
+      const uint32_t bR = static_cast<uint32_t>(cnt[2 * vmax + bi]);
+      const uint64_t bh = GEN == 2 ? 0ull : hreg.get(q, bR, mine && !PM);
       uint64_t cx =
-          mine ? seg_voxel_total<(GEN != 0)>(cnt, vmax, vb + sl, s, q, PM, unused, oob) : 0ull;
+          mine ? voxel_total_of<(GEN != 0)>(bx, bD, bN, bR, bh, s, q, PM, unused) : 0ull;
 #pragma unroll
       for (int o = 1; o < H; o <<= 1) {
         const uint64_t y = __shfl_up_sync(kFull, cx, o, H);
@@ -421,8 +478,9 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     const uint32_t N = static_cast<uint32_t>(cnt[vmax + vi]);
     const uint32_t R = static_cast<uint32_t>(cnt[2 * vmax + vi]);
     const uint32_t hm = dir_mask(v, s);
+    const uint64_t hR = GEN == 2 ? 0ull : hreg.get(q, R, act && !PM);
     uint64_t c0, c1, X;
-    voxel_terms<(GEN != 0)>(PM, q, v, s, D, N, R, act, c0, c1, X);
+    voxel_terms<(GEN != 0)>(PM, q, v, s, D, N, R, hR, c0, c1, X);
     const uint64_t C = chan_cum(cl, lk, q, c0, c1, D, N, R, X, hm);
     const uint64_t Cb = H == 8 ? chan_cum(cl2, lk2, q, c0, c1, D, N, R, X, hm) : ~0ull;
     uint64_t C16 = 0, C17 = 0, C18;
@@ -483,14 +541,24 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : 8) k_chi_seg(
     bool ovf = false;
     uint64_t dv, du;
     if (PRE) {
+      // lane 0 the new total of v, lane 1 that of u (the hop's target)
+      const int xv = (sl == 1 && u >= 0) ? u : v;
+      const int xi = static_cast<int>(TSG_IDX(xv, vmax, oob));
+      const uint32_t xD = static_cast<uint32_t>(cnt[xi]);
+      const uint32_t xN = static_cast<uint32_t>(cnt[vmax + xi]);
+      const uint32_t xR = static_cast<uint32_t>(cnt[2 * vmax + xi]);
+      const uint64_t xh = GEN == 2 ? 0ull : hreg.get(q, xR, act && !PM);
       const uint64_t a_new =
-          act ? seg_voxel_total<(GEN != 0)>(cnt, vmax, (sl == 1 && u >= 0) ? u : v, s, q, PM, ovf,
-                                             oob)
-              : 0ull;
+          act ? voxel_total_of<(GEN != 0)>(xv, xD, xN, xR, xh, s, q, PM, ovf) : 0ull;
       dv = __shfl_sync(kFull, a_new, 0, H) - a_old_v;
       du = __shfl_sync(kFull, a_new, 1, H) - a_old_u;
     } else {
-      dv = (act ? seg_voxel_total<(GEN != 0)>(cnt, vmax, v, s, q, PM, ovf, oob) : 0ull) - a_old_v;
+      const int vi2 = static_cast<int>(TSG_IDX(v, vmax, oob));
+      const uint32_t vD = static_cast<uint32_t>(cnt[vi2]);
+      const uint32_t vN = static_cast<uint32_t>(cnt[vmax + vi2]);
+      const uint32_t vR = static_cast<uint32_t>(cnt[2 * vmax + vi2]);
+      const uint64_t vh = GEN == 2 ? 0ull : hreg.get(q, vR, act && !PM);
+      dv = (act ? voxel_total_of<(GEN != 0)>(v, vD, vN, vR, vh, s, q, PM, ovf) : 0ull) - a_old_v;
       // one molecule of species hs arrived at u: the change of u's total in
       // closed form (the total is affine in D and N apart from k_in X)
       du = 0;

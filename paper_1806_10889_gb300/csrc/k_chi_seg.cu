@@ -91,7 +91,7 @@ cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint
   // held or reached a count above 65535 with 32-bit counts, from the state
   // they started the step with.
   const ChiSegKernel kn =
-      (redo && pre && gen == 0 && vmax_cells > 256) ? chi_seg_kernel_narrow(H, qb) : nullptr;
+      (redo && gen == 0 && vmax_cells > 256) ? chi_seg_kernel_narrow(H, pre, qb) : nullptr;
   if (!kn)
     return launch_one(k, d_views, d_items, n_items, nullptr, d_counter, seg_bytes, H,
                       warps_per_block, blocks, step_off, dt, nullptr, nullptr, stream);

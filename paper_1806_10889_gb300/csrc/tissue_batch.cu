@@ -50,14 +50,29 @@ struct tissue_batch {
   double graph_dt = 0.0;
   uint32_t steps_per_graph = 1;
   uint32_t scheme = TISSUE_SPLIT_LIE;
+  // timing (tissue_batch_set_timing): events at the step's start and end,
+  // before the well-mixed launch and after it, and after each class
+  bool timing = false, timed_once = false;
+  std::vector<cudaEvent_t> tev;  // [0] step start, [1] step end, [2] chi start, [3 + i] after part i
 };
 
 namespace {
 
+// Record timing event i on the batch stream (an event-record node when the
+// stream is being captured).
+int mark(tissue_batch* b, size_t i) {
+  if (!b->timing) return TISSUE_OK;
+  return cudaEventRecordWithFlags(b->tev[i], b->stream, cudaEventRecordExternal) == cudaSuccess
+             ? TISSUE_OK
+             : TISSUE_E_CUDA;
+}
+
 int chi_all(tissue_batch* b, double dt) {
+  if (mark(b, 2) != TISSUE_OK) return TISSUE_E_CUDA;
   if (b->n_wm && launch_chi_wm(b->d_views, b->d_items + b->wm_off, b->n_wm, b->wm_vmax, 0u, dt,
                                b->stream) != cudaSuccess)
     return TISSUE_E_CUDA;
+  if (mark(b, 3) != TISSUE_OK) return TISSUE_E_CUDA;
   for (size_t c = 0; c < b->classes.size(); ++c) {
     const ClassPlan& p = b->classes[c];
     uint32_t* counters = b->d_counters + 3 * c;
@@ -68,6 +83,7 @@ int chi_all(tissue_batch* b, double dt) {
                        static_cast<int>(p.lanes), static_cast<int>(p.warps_per_block), 0, 0u, dt,
                        p.layout == TISSUE_LAYOUT_PREFIX, p.gen, &redo, b->stream) != cudaSuccess)
       return TISSUE_E_CUDA;
+    if (mark(b, 4 + c) != TISSUE_OK) return TISSUE_E_CUDA;
   }
   return TISSUE_OK;
 }
@@ -82,6 +98,7 @@ int faces(tissue_batch* b, int axis, uint32_t tag, double dt) {
 
 int enqueue_step(tissue_batch* b, double dt) {
   int rc;
+  if ((rc = mark(b, 0))) return rc;
   if (b->scheme == TISSUE_SPLIT_LIE) {
     if ((rc = chi_all(b, dt)) || (rc = faces(b, 0, kTagSx, dt)) || (rc = faces(b, 1, kTagSy, dt)))
       return rc;
@@ -94,7 +111,14 @@ int enqueue_step(tissue_batch* b, double dt) {
   if (launch_advance_list(b->d_views, static_cast<uint32_t>(b->members.size()), b->stream) !=
       cudaSuccess)
     return TISSUE_E_CUDA;
+  if ((rc = mark(b, 1))) return rc;
+  if (b->timing) b->timed_once = true;
   return TISSUE_OK;
+}
+
+void drop_events(tissue_batch* b) {
+  for (cudaEvent_t e : b->tev) cudaEventDestroy(e);
+  b->tev.clear();
 }
 
 void drop_graph(tissue_batch* b) {
@@ -307,6 +331,63 @@ int tissue_batch_sync(tissue_batch* b) {
   return worst;
 }
 
+int tissue_batch_class_info(const tissue_batch* b, uint32_t i, uint32_t* V,
+                            uint32_t* lanes_per_cell, uint32_t* warps_per_block,
+                            uint32_t* smem_layout, uint32_t* cells) {
+  if (!b || i >= b->classes.size()) return TISSUE_E_ARG;
+  const ClassPlan& p = b->classes[i];
+  if (V) *V = p.V;
+  if (lanes_per_cell) *lanes_per_cell = p.lanes;
+  if (warps_per_block) *warps_per_block = p.warps_per_block;
+  if (smem_layout) *smem_layout = p.layout;
+  if (cells) *cells = p.n_items;
+  return TISSUE_OK;
+}
+
+int tissue_batch_set_timing(tissue_batch* b, uint32_t on) {
+  if (!b || on > 1) return TISSUE_E_ARG;
+  if ((on != 0) == b->timing) return TISSUE_OK;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  drop_graph(b);
+  drop_events(b);
+  b->timing = false;
+  b->timed_once = false;
+  if (!on) return TISSUE_OK;
+  const size_t n = 4 + b->classes.size();
+  for (size_t i = 0; i < n; ++i) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      drop_events(b);
+      return TISSUE_E_CUDA;
+    }
+    b->tev.push_back(e);
+  }
+  b->timing = true;
+  return TISSUE_OK;
+}
+
+int tissue_batch_read_timing(tissue_batch* b, double* step_ms, double* wm_ms, double* class_ms,
+                             uint32_t n) {
+  if (!b || !b->timing || !b->timed_once || n > b->classes.size()) return TISSUE_E_ARG;
+  if (n > 0 && !class_ms) return TISSUE_E_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  float ms = 0.0f;
+  if (step_ms) {
+    if (cudaEventElapsedTime(&ms, b->tev[0], b->tev[1]) != cudaSuccess) return TISSUE_E_CUDA;
+    *step_ms = ms;
+  }
+  if (wm_ms) {
+    if (cudaEventElapsedTime(&ms, b->tev[2], b->tev[3]) != cudaSuccess) return TISSUE_E_CUDA;
+    *wm_ms = ms;
+  }
+  for (uint32_t i = 0; i < n; ++i) {
+    if (cudaEventElapsedTime(&ms, b->tev[3 + i], b->tev[4 + i]) != cudaSuccess)
+      return TISSUE_E_CUDA;
+    class_ms[i] = ms;
+  }
+  return TISSUE_OK;
+}
+
 int tissue_batch_info(const tissue_batch* b, uint32_t* n_members, uint32_t* n_classes,
                       uint64_t* n_cells) {
   if (!b) return TISSUE_E_ARG;
@@ -324,6 +405,7 @@ void tissue_batch_destroy(tissue_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
+  drop_events(b);
   cudaFree(b->dmem);
   delete b;
 }

@@ -128,7 +128,7 @@ ChiSegKernel chi_seg_kernel_nd(int H, bool pre, bool qb);   // k_chi_seg.cu
 ChiSegKernel chi_seg_kernel_gen(int H, bool pre, bool qb);  // k_chi_seg_gen.cu
 ChiSegKernel chi_seg_kernel_pm(int H, bool pre, bool qb);   // k_chi_seg_pm.cu
 // 16-bit counts, prefix layout, Notch-Delta only; nullptr where not built.
-ChiSegKernel chi_seg_kernel_narrow(int H, bool qb);          // k_chi_seg_narrow.cu
+ChiSegKernel chi_seg_kernel_narrow(int H, bool pre, bool qb);  // k_chi_seg_narrow.cu
 uint32_t seg_bytes_for(uint32_t V, int H, bool pre, bool narrow = false);
 // Well-mixed cells (k_chi_wm.cu): one warp per (tissue, cell) item;
 // vmax_cells is the largest V among the listed cells.

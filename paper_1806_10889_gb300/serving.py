@@ -97,6 +97,10 @@ class Server:
         self.used = 0
         self.peak_used = 0
         self.device_events = 0
+        # batch rebuilds on membership changes and the host time they took
+        # (the batch's tables; its graph is captured on its first step)
+        self.rebuilds = 0
+        self.rebuild_s = 0.0
         self._cancel: set = set()
         self._cancel_lock = threading.Lock()
 
@@ -172,7 +176,9 @@ class Server:
             # 2. the round's requests; the batch follows them
             chosen = self._choose(active)
             key = tuple(id(t) for a in chosen for t in a.tissues)
-            if key != members_key:
+            rebuilt = key != members_key
+            if rebuilt:
+                tb = self.clock()
                 if batch is not None:
                     batch.close()
                 batch = Batch([t for a in chosen for t in a.tissues])
@@ -180,10 +186,21 @@ class Server:
                     from .autotune import apply_batch
                     apply_batch(batch, self.tuned)
                 members_key = key
+                self.rebuilds += 1
+                self.rebuild_s += self.clock() - tb
             # 3. one chunk, bounded by the chosen request that finishes first
             dt = chosen[0].req.dt
             k = min(self.chunk, min(a.req.n_steps - a.steps_done for a in chosen))
-            batch.step(dt, k)
+            if rebuilt:
+                # the first step of a new batch captures its graph: count the
+                # host time of that capture as rebuild time too
+                tb = self.clock()
+                batch.step(dt, 1)
+                self.rebuild_s += self.clock() - tb
+                if k > 1:
+                    batch.step(dt, k - 1)
+            else:
+                batch.step(dt, k)
             batch.sync()
             for a in chosen:
                 a.steps_done += k

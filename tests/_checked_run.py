@@ -64,7 +64,7 @@ def main():
     x[1, 0, 0] = 70000
     x[4, 0, 5] = 65000
     x[4, 2, 5] = 0xFFFF
-    for cfg in (None, (P, 16, 2, 0, PRE), (P, 8, 2, 0, PRE)):
+    for cfg in (None, (P, 16, 2, 0, PRE), (P, 8, 2, 0, PRE), (P, 32, 2, 0, REC)):
         same(big, 0.05, 2, cfg, x0=x.ravel())
     model = W.promoter_model(8)
     model["kd"] = 3.0

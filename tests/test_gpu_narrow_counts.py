@@ -23,7 +23,7 @@ if not torch.cuda.is_available():
 from paper_1806_10889_gb300 import tissue as T  # noqa: E402
 from paper_1806_10889_gb300.tissue import Tissue  # noqa: E402
 
-P, PRE = T.KERNEL_PERSISTENT, T.LAYOUT_PREFIX
+P, PRE, REC = T.KERNEL_PERSISTENT, T.LAYOUT_PREFIX, T.LAYOUT_RECOMPUTE
 LIMIT = 0xFFFF  # the largest count the 16-bit layout holds
 
 # D does not hop, and R -> D + N (k_off) releases D faster than it decays:
@@ -81,7 +81,8 @@ def test_counts_above_16_bits_are_redone_bit_exact(n):
 
 
 @pytest.mark.parametrize("config", [(P, 32, 2, 0, PRE), (P, 32, 1, 3, PRE), (P, 16, 4, 0, PRE),
-                                    (P, 16, 1, 1, PRE), (P, 8, 2, 0, PRE), (P, 8, 1, 0, PRE)])
+                                    (P, 16, 1, 1, PRE), (P, 8, 2, 0, PRE), (P, 8, 1, 0, PRE),
+                                    (P, 32, 2, 0, REC), (P, 32, 4, 0, REC), (P, 32, 1, 3, REC)])
 def test_every_launch_shape_with_16_bit_counts(config):
     spec = TissueSpec(3, 2, 32, seed=73, tissue_id=1).with_model(**RELEASE)
     _, crossed = _run(spec, _big_state(spec), 0.05, 2, config)
@@ -103,7 +104,9 @@ def test_batch_shares_the_redo_list_across_classes():
         t.write_counts(x, 0)
     b = Batch(members)
     dt = 0.05
-    for k in range(2):
+    for k in range(4):
+        if k == 2:  # then the large-cell class with the counts-only layout
+            b.set_class_launch(1024, 32, 2, REC)
         b.step(dt, 1)
         b.sync()
         for i, s in enumerate(specs):

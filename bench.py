@@ -75,8 +75,14 @@ CHI_SOURCES = ["chi_seg.cuh", "tissue_dev.cuh", "tissue_internal.h", "k_chi_seg.
 # `sources` is chi_sources_sha() of the kernel they were measured on: when the
 # kernel changes, the figures are stale and the roofline reports none.
 CHI_IPE = {
-    "sources": None,
-    "kernels": {},
+    "sources": "61e143ea42c52fb3",
+    "kernels": {
+        "batch:H32/pre/qb0/nd/u16": (543.6, 0.6820),
+        "batch:H16/pre/qb0/nd/u32": (301.5, 0.4484),
+        "batch:H8/pre/qb0/nd/u32": (170.2, 0.5329),
+        "medium:H16/pre/qb0/nd/u32": (297.0, 0.3141),
+        "large:H32/pre/qb0/nd/u16": (542.7, 1.3177),
+    },
 }
 
 

@@ -107,3 +107,39 @@ def test_batch_rejects_bad_input():
         b.set_class_launch(64, 4, 2, 1)  # lanes must be 16 or 32
     b.close()
     a.close()
+
+
+def test_batch_timing_and_class_info_change_no_result():
+    """Per-class timing (event-record nodes in the captured graph) reports
+    positive times that add up within the step, and the trajectory is the
+    same with timing on and off."""
+    outs = []
+    for timing in (False, True):
+        members = [T.Tissue(s) for s in MIX]
+        b = Batch(members)
+        cls = b.classes()
+        assert [c["V"] for c in cls] == [1024, 256, 100, 64]
+        assert sum(c["cells"] for c in cls) == sum(s.cells for s in MIX)
+        for c in cls:
+            assert c["lanes_per_cell"] in (8, 16, 32) and c["smem_layout"] in (0, 1)
+        if timing:
+            b.set_timing(True)
+            with pytest.raises(T.TissueError):
+                b.read_timing()  # no timed step yet
+        for _ in range(3):
+            b.step(0.1, 1)
+            if timing:
+                step_ms, wm_ms, class_ms = b.read_timing()
+                assert step_ms > 0 and wm_ms >= 0 and len(class_ms) == len(cls)
+                assert all(x > 0 for x in class_ms)
+                assert sum(class_ms) + wm_ms <= step_ms * 1.001
+        b.sync()
+        outs.append([m.read_counts() for m in members])
+        if timing:
+            b.set_timing(False)
+            with pytest.raises(T.TissueError):
+                b.read_timing()
+        b.close()
+        for m in members:
+            m.close()
+    assert all(np.array_equal(x, y) for x, y in zip(*outs))

@@ -1,7 +1,8 @@
 """The GPU against the oracle from burned-in states, where the benchmarks time
-their steps: molecule counts in the hundreds per voxel instead of the initial
-Poisson(5), so the Hill-table range, the small-count fast path of the voxel
-totals and the 16-bit counts of large cells all run in their working regime.
+their steps: tens of molecules per voxel (about 60 D, 30 N and 10 R in the
+medium tissue after 20 time units) instead of the initial Poisson(5), so the
+Hill values, the small-count fast path of the voxel totals and the 16-bit
+counts of large cells all run in their working regime.
 
 The GPU advances the workload alone; its state is then handed both to a fresh
 tissue (tissue_write_counts, checkpoint resume) and to the oracle, and the
@@ -54,7 +55,7 @@ def test_medium_tissue_after_200_steps_matches_oracle():
     assert k0 == 200
     # the burn-in reached the working regime: far above the initial mean of 5
     per_voxel = state.reshape(spec.cells, 3, spec.V).mean(axis=(0, 2))
-    assert per_voxel[0] > 50 and per_voxel[1] > 30, per_voxel
+    assert per_voxel[0] > 40 and per_voxel[1] > 20, per_voxel
     resumed = Tissue(spec)
     resumed.write_counts(state, step_index=k0)
     d, m = orc_desc(spec), orc_model(spec)

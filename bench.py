@@ -77,11 +77,17 @@ CHI_SOURCES = ["chi_seg.cuh", "tissue_dev.cuh", "tissue_internal.h", "k_chi_seg.
 CHI_IPE = {
     "sources": "61e143ea42c52fb3",
     "kernels": {
-        "batch:H32/pre/qb0/nd/u16": (543.6, 0.6820),
-        "batch:H16/pre/qb0/nd/u32": (301.5, 0.4484),
-        "batch:H8/pre/qb0/nd/u32": (170.2, 0.5329),
-        "medium:H16/pre/qb0/nd/u32": (297.0, 0.3141),
-        "large:H32/pre/qb0/nd/u16": (542.7, 1.3177),
+        "batch:V1024/H32/pre/qb0/nd/u16": (543.6, 0.6820),
+        "batch:V256/H16/pre/qb0/nd/u32": (301.5, 0.4484),
+        "batch:V64/H8/pre/qb0/nd/u32": (170.2, 0.5329),
+        "batch:V1024/H16/pre/qb1/nd/u16": (361.1, 0.6840),
+        "batch:V1024/H32/rec/qb0/nd/u16": (628.6, 0.6826),
+        "batch:V256/H8/pre/qb1/nd/u32": (206.5, 0.4485),
+        "batch:V256/H32/pre/qb0/nd/u32": (551.6, 0.4491),
+        "batch:V64/H16/pre/qb0/nd/u32": (305.1, 0.5346),
+        "batch:V64/H32/pre/qb0/nd/u32": (551.9, 0.5363),
+        "medium:V256/H16/pre/qb0/nd/u32": (297.0, 0.3141),
+        "large:V1024/H32/pre/qb0/nd/u16": (542.7, 1.3177),
     },
 }
 
@@ -98,11 +104,12 @@ def chi_sources_sha() -> str:
 
 
 def chi_kernel_key(V: int, lanes: int, layout: int, model: str = "nd") -> str:
-    """The instantiation the launcher picks for cells of V voxels."""
-    pre = layout == 0
+    """The cell size and the kernel instantiation the launcher picks for it
+    (the instructions per event depend on both)."""
     qb = V > lanes * lanes
-    narrow = pre and model == "nd" and V > 256
-    return f"H{lanes}/{'pre' if pre else 'rec'}/qb{int(qb)}/{model}/{'u16' if narrow else 'u32'}"
+    narrow = model == "nd" and V > 256
+    return (f"V{V}/H{lanes}/{'pre' if layout == 0 else 'rec'}/qb{int(qb)}/{model}/"
+            f"{'u16' if narrow else 'u32'}")
 
 
 def chi_ipe(workload: str, key: str):
@@ -394,7 +401,8 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
     roofline["class_V"] = per_class[dom]["V"]
 
     # end to end through the C ABI: every tissue's state from pinned host
-    # memory before each step, back to pinned host memory after it
+    # memory before each step, back to pinned host memory after it (the
+    # batch's state I/O: all copies queued on the batch stream, one wait)
     e2e = None
     hosts = [torch.empty(m.spec.state_ints, dtype=torch.int32, pin_memory=True) for m in members]
     for m, h in zip(members, hosts):
@@ -407,12 +415,9 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(args.e2e_steps):
-            for m, h in zip(members, hosts):
-                m.write_counts_from(h, step_index=k0 + i)
+            bt.write_counts(hosts, step_index=k0 + i)  # H2D of every member's input state
             bt.step(dt, 1)
-            bt.sync()
-            for m, h in zip(members, hosts):
-                m.read_counts_into(h)
+            bt.read_counts(hosts)                      # D2H of every member's result
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         e_ev = float((_events(members) - e0).sum())
@@ -900,6 +905,9 @@ def run_profile(args) -> dict:
     torch.cuda.synchronize()
     if args.profile_chi == "batch":
         bt = Batch(members)
+        for part in args.profile_class:  # V:lanes:warps:layout, e.g. an autotuner pick
+            V, lanes, wpb, layout = (int(x) for x in part.split(":"))
+            bt.set_class_launch(V, lanes, wpb, layout)
         classes = bt.classes()
         step = bt.step
 
@@ -1100,6 +1108,8 @@ def main():
     ap.add_argument("--profile-chi", choices=["batch", "medium", "large"], default=None,
                     help="profiling case: step this workload, printing each chi launch class's "
                          "events per step for ncu's per-launch counters")
+    ap.add_argument("--profile-class", action="append", default=[],
+                    help="with --profile-chi batch: V:lanes:warps:layout launch of one class")
     ap.add_argument("--wavefront", action="store_true",
                     help="bound the gain of a barrier-free wavefront across --steps steps of "
                          "the medium tissue (per-cell events read back every step)")

@@ -270,6 +270,27 @@ int tissue_batch_sync(tissue_batch* b);
 int tissue_batch_info(const tissue_batch* b, uint32_t* n_members, uint32_t* n_classes,
                       uint64_t* n_cells);
 
+/* State I/O of a whole batch: the batch form of tissue_write_counts and
+ * tissue_read_counts (in the paper the modules hand each cell's state on
+ * through files every step, Sec. II-B; these calls move the states of all
+ * members between host and device memory instead), with every member's copy
+ * queued on the batch stream and one wait for all of them.
+ * host[i] (count entries, i in member order): member i's state, exactly
+ * width*height*3*V int32 in the layout of tissue_read_counts; pinned host
+ * memory makes the copies asynchronous DMA.  The caller owns the arrays. */
+
+/* Write every member's state; step_index[i] (or NULL: unchanged) becomes
+ * member i's global step index.  After the copies one device pass checks
+ * every count lies in [0, TISSUE_COUNT_MAX], and the members' device error
+ * flags are cleared; the call waits for all of it.  TISSUE_E_ARG if a count
+ * is out of range (the members' states are then unspecified). */
+int tissue_batch_write_counts(tissue_batch* b, const int32_t* const* host,
+                              const uint32_t* step_index);
+
+/* Copy every member's state to host[i] and wait; reports the first member's
+ * latched device error in member order, as tissue_read_counts does. */
+int tissue_batch_read_counts(tissue_batch* b, int32_t* const* host);
+
 /* Cell-size class i (0 <= i < n_classes of tissue_batch_info; largest cells
  * first): its cell size V, the launch shape of its chi launch and its number
  * of lattice cells (any pointer may be NULL). */

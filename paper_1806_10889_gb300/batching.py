@@ -52,6 +52,34 @@ class Batch:
                "tissue_batch_info")
         return int(a.value), int(b.value), int(c.value)
 
+    def write_counts(self, host_tensors, step_index=None) -> None:
+        """Every member's state from host memory (torch int32 CPU tensors,
+        pinned for asynchronous copies), in member order; step_index: one int
+        for all members, a list, or None to keep each member's index."""
+        n = len(self.members)
+        if len(host_tensors) != n:
+            raise ValueError("one host array per member")
+        for t, m in zip(host_tensors, self.members):
+            if t.numel() != m.spec.state_ints or t.dtype != __import__("torch").int32:
+                raise ValueError("each host array must be the member's int32 state")
+        ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in host_tensors])
+        steps = None
+        if step_index is not None:
+            vals = [int(step_index)] * n if isinstance(step_index, int) else list(step_index)
+            steps = (C.c_uint32 * n)(*vals)
+        _check(lib().tissue_batch_write_counts(self._h, ptrs, steps), "tissue_batch_write_counts")
+
+    def read_counts(self, host_tensors) -> None:
+        """Every member's state into host memory (torch int32 CPU tensors)."""
+        n = len(self.members)
+        if len(host_tensors) != n:
+            raise ValueError("one host array per member")
+        for t, m in zip(host_tensors, self.members):
+            if t.numel() != m.spec.state_ints or t.dtype != __import__("torch").int32:
+                raise ValueError("each host array must be the member's int32 state")
+        ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in host_tensors])
+        _check(lib().tissue_batch_read_counts(self._h, ptrs), "tissue_batch_read_counts")
+
     def classes(self) -> list[dict]:
         """Cell-size classes, largest cells first: V, launch shape, cells."""
         n = self.info()[1]

@@ -170,6 +170,49 @@ __global__ void k_advance_list(const TissueView* __restrict__ views, const uint3
   if (i < n) *const_cast<uint32_t*>(views[i].step) += 1u;
 }
 
+// Batch checkpoint writes: every member's step counter from steps[] (if
+// given) and its error flag cleared.
+__global__ void k_set_steps_list(const TissueView* __restrict__ views, const uint32_t* steps,
+                                 const uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (steps) *const_cast<uint32_t*>(views[i].step) = steps[i];
+  *views[i].err = 0;
+}
+
+// Set *bad if any count of any member lies outside [0, TISSUE_COUNT_MAX]
+// (one unsigned compare: a negative int32 is a large unsigned value).  Blocks
+// stride over the members (y) and over each member's state (x), 16 bytes per
+// load where the state allows it.
+__global__ void k_check_counts_list(const TissueView* __restrict__ views, const uint32_t n,
+                                    int* bad) {
+  for (uint32_t m = blockIdx.y; m < n; m += gridDim.y) {
+    const TissueView& t = views[m];
+    const uint64_t total = static_cast<uint64_t>(t.width) * t.height * 3 * t.V;
+    const uint32_t* c = reinterpret_cast<const uint32_t*>(t.counts);
+    uint32_t worst = 0;
+    const uint64_t n4 = total >> 2;  // the buffer is 16-byte aligned
+    const uint4* c4 = reinterpret_cast<const uint4*>(c);
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n4;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+      const uint4 x = c4[i];
+      worst = max(worst, max(max(x.x, x.y), max(x.z, x.w)));
+    }
+    for (uint64_t i = (n4 << 2) + blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+         i < total; i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+      worst = max(worst, c[i]);
+    if (__any_sync(kFull, worst > static_cast<uint32_t>(kCountMax)) && (threadIdx.x & 31) == 0)
+      atomicOr(bad, 1);
+  }
+}
+
+// Every member's error flag into out[] (one copy back for the whole batch).
+__global__ void k_gather_err_list(const TissueView* __restrict__ views, const uint32_t n,
+                                  int* out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = *views[i].err;
+}
+
 // Initial counts: Poisson(lambda_s) per voxel and species by inversion,
 // accumulating p_k = p_{k-1} * lambda / k; p0 = exp(-lambda) from the host.
 __global__ void k_init(const TissueView t, const double p0_0, const double p0_1, const double p0_2,
@@ -231,6 +274,28 @@ cudaError_t launch_sig_list(const TissueView* d_views, const uint2* d_items, uin
 cudaError_t launch_advance_list(const TissueView* d_views, uint32_t n, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   k_advance_list<<<(n + 255) / 256, 256, 0, stream>>>(d_views, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_steps_list(const TissueView* d_views, const uint32_t* d_steps, uint32_t n,
+                                  cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  k_set_steps_list<<<(n + 255) / 256, 256, 0, stream>>>(d_views, d_steps, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_counts_list(const TissueView* d_views, uint32_t n, int* d_bad,
+                                     cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const dim3 grid(16, n < 65535u ? n : 65535u);
+  k_check_counts_list<<<grid, 256, 0, stream>>>(d_views, n, d_bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_err_list(const TissueView* d_views, uint32_t n, int* d_out,
+                                   cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  k_gather_err_list<<<(n + 255) / 256, 256, 0, stream>>>(d_views, n, d_out);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,9 @@ struct tissue_batch {
   uint2* d_items = nullptr;   // chi items of every class, then x-faces, then y-faces
   uint32_t* d_counters = nullptr;  // per class: work counter, redo count, redo-pass work counter
   uint2* d_redo = nullptr;         // cells a class's 16-bit-count pass gives up on
+  uint32_t* d_io_steps = nullptr;  // checkpoint writes: the members' new step indices
+  int* d_io_err = nullptr;         // checkpoint reads: the members' error flags
+  int* d_io_bad = nullptr;         // checkpoint writes: a count out of range
   size_t xface_off = 0, yface_off = 0, wm_off = 0;
   uint32_t n_xfaces = 0, n_yfaces = 0;
   uint32_t n_wm = 0, wm_vmax = 0;  // well-mixed cells of all members (one launch)
@@ -203,8 +206,10 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
   size_t redo_items = 0;  // the classes run one after another and share the redo list
   for (const ClassPlan& p : b->classes) redo_items = std::max<size_t>(redo_items, p.n_items);
   const size_t redo_bytes = (sizeof(uint2) * redo_items + 255) & ~static_cast<size_t>(255);
-  const size_t total =
-      views_bytes + items_bytes + redo_bytes + 3 * sizeof(uint32_t) * b->classes.size();
+  const size_t io_bytes = (2 * sizeof(uint32_t) * count + 255) & ~static_cast<size_t>(255);
+  const size_t counters_bytes =
+      (3 * sizeof(uint32_t) * b->classes.size() + 255) & ~static_cast<size_t>(255);
+  const size_t total = views_bytes + items_bytes + redo_bytes + counters_bytes + io_bytes + 256;
   if (lib_malloc(reinterpret_cast<void**>(&b->dmem), total) != cudaSuccess) {
     cudaGetLastError();
     delete b;
@@ -214,6 +219,10 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
   b->d_items = reinterpret_cast<uint2*>(b->dmem + views_bytes);
   b->d_redo = reinterpret_cast<uint2*>(b->dmem + views_bytes + items_bytes);
   b->d_counters = reinterpret_cast<uint32_t*>(b->dmem + views_bytes + items_bytes + redo_bytes);
+  unsigned char* io = b->dmem + views_bytes + items_bytes + redo_bytes + counters_bytes;
+  b->d_io_steps = reinterpret_cast<uint32_t*>(io);
+  b->d_io_err = reinterpret_cast<int*>(io + sizeof(uint32_t) * count);
+  b->d_io_bad = reinterpret_cast<int*>(io + io_bytes);
   std::vector<TissueView> views(count);
   for (uint32_t i = 0; i < count; ++i) views[i] = info[i].view;
   // Members' pending work (creation, earlier steps) must finish before the
@@ -329,6 +338,63 @@ int tissue_batch_sync(tissue_batch* b) {
     if (rc != TISSUE_OK) worst = rc;
   }
   return worst;
+}
+
+int tissue_batch_write_counts(tissue_batch* b, const int32_t* const* host,
+                              const uint32_t* step_index) {
+  NvtxRange range("tissue_batch_write_counts");
+  if (!b || !host) return TISSUE_E_ARG;
+  const uint32_t n = static_cast<uint32_t>(b->members.size());
+  for (uint32_t i = 0; i < n; ++i)
+    if (!host[i]) return TISSUE_E_ARG;
+  for (uint32_t i = 0; i < n; ++i) {
+    TissueInfo info;
+    if (!tissue_info(b->members[i], &info)) return TISSUE_E_ARG;
+    if (cudaMemcpyAsync(info.view.counts, host[i], tissue_state_bytes(&info.desc),
+                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+      return TISSUE_E_CUDA;
+  }
+  if (step_index && cudaMemcpyAsync(b->d_io_steps, step_index, sizeof(uint32_t) * n,
+                                    cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  if (cudaMemsetAsync(b->d_io_bad, 0, sizeof(int), b->stream) != cudaSuccess ||
+      launch_set_steps_list(b->d_views, step_index ? b->d_io_steps : nullptr, n, b->stream) !=
+          cudaSuccess ||
+      launch_check_counts_list(b->d_views, n, b->d_io_bad, b->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  int bad = 0;
+  if (cudaMemcpyAsync(&bad, b->d_io_bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  if (step_index)
+    for (uint32_t i = 0; i < n; ++i) tissue_set_host_step(b->members[i], step_index[i]);
+  return bad ? TISSUE_E_ARG : TISSUE_OK;
+}
+
+int tissue_batch_read_counts(tissue_batch* b, int32_t* const* host) {
+  NvtxRange range("tissue_batch_read_counts");
+  if (!b || !host) return TISSUE_E_ARG;
+  const uint32_t n = static_cast<uint32_t>(b->members.size());
+  for (uint32_t i = 0; i < n; ++i)
+    if (!host[i]) return TISSUE_E_ARG;
+  for (uint32_t i = 0; i < n; ++i) {
+    TissueInfo info;
+    if (!tissue_info(b->members[i], &info)) return TISSUE_E_ARG;
+    if (cudaMemcpyAsync(host[i], info.view.counts, tissue_state_bytes(&info.desc),
+                        cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+      return TISSUE_E_CUDA;
+  }
+  if (launch_gather_err_list(b->d_views, n, b->d_io_err, b->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  std::vector<int> err(n);
+  if (cudaMemcpyAsync(err.data(), b->d_io_err, sizeof(int) * n, cudaMemcpyDeviceToHost,
+                      b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return TISSUE_E_CUDA;
+  for (int e : err)
+    if (e) return error_code_of(e);
+  return TISSUE_OK;
 }
 
 int tissue_batch_class_info(const tissue_batch* b, uint32_t i, uint32_t* V,

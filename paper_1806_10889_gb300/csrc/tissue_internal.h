@@ -127,7 +127,8 @@ using ChiSegKernel = void (*)(const TissueView*, const uint2*, uint32_t, uint32_
 ChiSegKernel chi_seg_kernel_nd(int H, bool pre, bool qb);   // k_chi_seg.cu
 ChiSegKernel chi_seg_kernel_gen(int H, bool pre, bool qb);  // k_chi_seg_gen.cu
 ChiSegKernel chi_seg_kernel_pm(int H, bool pre, bool qb);   // k_chi_seg_pm.cu
-// 16-bit counts, prefix layout, Notch-Delta only; nullptr where not built.
+// 16-bit counts, Notch-Delta only (prefix layout at 8, 16 or 32 lanes; the
+// counts-only layout at 32 lanes); nullptr where not built.
 ChiSegKernel chi_seg_kernel_narrow(int H, bool pre, bool qb);  // k_chi_seg_narrow.cu
 uint32_t seg_bytes_for(uint32_t V, int H, bool pre, bool narrow = false);
 // Well-mixed cells (k_chi_wm.cu): one warp per (tissue, cell) item;
@@ -137,6 +138,14 @@ cudaError_t launch_chi_wm(const TissueView* d_views, const uint2* d_items, uint3
 cudaError_t launch_sig_list(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
                             int axis, uint32_t tag, double dt, cudaStream_t stream);
 cudaError_t launch_advance_list(const TissueView* d_views, uint32_t n, cudaStream_t stream);
+// Batch checkpoint I/O (k_sig.cu): set step counters (d_steps may be null) and
+// clear error flags; flag a count outside [0, kCountMax]; gather error flags.
+cudaError_t launch_set_steps_list(const TissueView* d_views, const uint32_t* d_steps, uint32_t n,
+                                  cudaStream_t stream);
+cudaError_t launch_check_counts_list(const TissueView* d_views, uint32_t n, int* d_bad,
+                                     cudaStream_t stream);
+cudaError_t launch_gather_err_list(const TissueView* d_views, uint32_t n, int* d_out,
+                                   cudaStream_t stream);
 
 // Library-internal access to a tissue handle (tissue_lib.cu).
 struct TissueInfo {
@@ -151,6 +160,9 @@ bool tissue_info(const tissue* t, TissueInfo* out);
 constexpr uint64_t kFewCells = 1024;
 tissue_launch default_launch(uint32_t V, uint64_t cells);
 void tissue_advance_host_step(tissue* t, uint32_t n);
+void tissue_set_host_step(tissue* t, uint32_t step_index);
+// A latched device error flag as the C ABI's status code.
+int error_code_of(int flag);
 int seg_lanes_for(uint32_t V, int want);
 
 // tag: the Philox stream tag of this face phase (kTagSx, kTagSy, kTagSx2, kTagSy2).

@@ -209,10 +209,7 @@ int device_error(tissue* t) {
   if (cudaMemcpyAsync(&h, t->d_err, sizeof(int), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess)
     return TISSUE_E_CUDA;
   if (cudaStreamSynchronize(t->stream) != cudaSuccess) return TISSUE_E_CUDA;
-  if (h & kErrBounds) return TISSUE_E_BOUNDS;
-  if (h & kErrInternal) return TISSUE_E_CUDA;
-  if (h & kErrState) return TISSUE_E_STATE;
-  return h ? TISSUE_E_OVERFLOW : TISSUE_OK;
+  return tsg::error_code_of(h);
 }
 
 // The one-warp-per-cell kernel computes lattice cells of the Notch-Delta
@@ -300,6 +297,15 @@ bool tsg::tissue_info(const tissue* t, TissueInfo* out) {
 }
 
 void tsg::tissue_advance_host_step(tissue* t, uint32_t n) { t->step_index += n; }
+
+void tsg::tissue_set_host_step(tissue* t, uint32_t step_index) { t->step_index = step_index; }
+
+int tsg::error_code_of(int h) {
+  if (h & kErrBounds) return TISSUE_E_BOUNDS;
+  if (h & kErrInternal) return TISSUE_E_CUDA;
+  if (h & kErrState) return TISSUE_E_STATE;
+  return h ? TISSUE_E_OVERFLOW : TISSUE_OK;
+}
 
 extern "C" {
 

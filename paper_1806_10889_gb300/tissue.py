@@ -107,6 +107,8 @@ SIGNATURES = {
     "tissue_batch_set_schedule": (C.c_int, [C.c_void_p, C.c_uint32]),
     "tissue_batch_sync": (C.c_int, [C.c_void_p]),
     "tissue_batch_info": (C.c_int, [C.c_void_p, _P(C.c_uint32), _P(C.c_uint32), _P(C.c_uint64)]),
+    "tissue_batch_write_counts": (C.c_int, [C.c_void_p, _P(C.c_void_p), _P(C.c_uint32)]),
+    "tissue_batch_read_counts": (C.c_int, [C.c_void_p, _P(C.c_void_p)]),
     "tissue_batch_class_info": (C.c_int, [C.c_void_p, C.c_uint32, _P(C.c_uint32),
                                           _P(C.c_uint32), _P(C.c_uint32), _P(C.c_uint32),
                                           _P(C.c_uint32)]),

@@ -35,10 +35,11 @@ def test_wavefront_bound_is_zero_when_one_cell_is_slowest_every_step():
 
 
 def test_chi_kernel_keys():
-    assert bench.chi_kernel_key(1024, 32, 0) == "H32/pre/qb0/nd/u16"
-    assert bench.chi_kernel_key(1024, 16, 0) == "H16/pre/qb1/nd/u16"
-    assert bench.chi_kernel_key(256, 16, 0) == "H16/pre/qb0/nd/u32"
-    assert bench.chi_kernel_key(64, 8, 1) == "H8/rec/qb0/nd/u32"
+    assert bench.chi_kernel_key(1024, 32, 0) == "V1024/H32/pre/qb0/nd/u16"
+    assert bench.chi_kernel_key(1024, 16, 0) == "V1024/H16/pre/qb1/nd/u16"
+    assert bench.chi_kernel_key(1024, 32, 1) == "V1024/H32/rec/qb0/nd/u16"
+    assert bench.chi_kernel_key(256, 16, 0) == "V256/H16/pre/qb0/nd/u32"
+    assert bench.chi_kernel_key(64, 8, 1) == "V64/H8/rec/qb0/nd/u32"
 
 
 def test_instruction_counts_were_measured_on_the_current_kernel():
@@ -47,8 +48,9 @@ def test_instruction_counts_were_measured_on_the_current_kernel():
     assert bench.CHI_IPE["sources"] == bench.chi_sources_sha(), (
         "the persistent chi kernel changed since its instructions per event were measured: "
         "re-run the ncu commands in profiles/k_chi_inst_per_event_by_cell_size.md")
-    for key in ("batch:H32/pre/qb0/nd/u16", "batch:H16/pre/qb0/nd/u32", "batch:H8/pre/qb0/nd/u32",
-                "medium:H16/pre/qb0/nd/u32", "large:H32/pre/qb0/nd/u16"):
+    for key in ("batch:V1024/H32/pre/qb0/nd/u16", "batch:V256/H16/pre/qb0/nd/u32",
+                "batch:V64/H8/pre/qb0/nd/u32", "medium:V256/H16/pre/qb0/nd/u32",
+                "large:V1024/H32/pre/qb0/nd/u16"):
         ipe, bpe = bench.CHI_IPE["kernels"][key]
         assert 100 < ipe < 1000 and 0 < bpe < 10
 

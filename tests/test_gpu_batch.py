@@ -143,3 +143,42 @@ def test_batch_timing_and_class_info_change_no_result():
         for m in members:
             m.close()
     assert all(np.array_equal(x, y) for x, y in zip(*outs))
+
+
+def test_batch_state_io_matches_per_member_io():
+    """tissue_batch_write_counts / read_counts: the same states and step
+    indices as the per-member calls, a count out of range rejected, and the
+    batch steps on from written states as the members would alone."""
+    members = [T.Tissue(s) for s in MIX]
+    b = Batch(members)
+    b.step(0.1, 2)
+    b.sync()
+    hosts = [torch.empty(s.state_ints, dtype=torch.int32, pin_memory=True) for s in MIX]
+    b.read_counts(hosts)
+    for h, m in zip(hosts, members):
+        assert np.array_equal(h.numpy(), m.read_counts())
+    # write back perturbed states at a new step index; step on both ways
+    rng = np.random.default_rng(4)
+    for h in hosts:
+        h.copy_(torch.from_numpy(rng.integers(0, 40, size=h.numel(), dtype=np.int32)))
+    alone = [T.Tissue(s) for s in MIX]
+    for t, h in zip(alone, hosts):
+        t.write_counts(h.numpy(), step_index=11)
+    b.write_counts(hosts, step_index=11)
+    assert all(m.get_step() == 11 for m in members)
+    b.step(0.1, 2)
+    b.read_counts(hosts)
+    for t, h in zip(alone, hosts):
+        t.step(0.1, 2)
+        assert np.array_equal(t.read_counts(), h.numpy())
+        t.close()
+    # a negative count and one above TISSUE_COUNT_MAX are rejected
+    for bad in (-1, 2 ** 30):
+        h0 = hosts[0].clone().pin_memory()
+        h0[5] = bad
+        with pytest.raises(T.TissueError) as e:
+            b.write_counts([h0] + hosts[1:], step_index=[0] * len(MIX))
+        assert e.value.code == T.E_ARG
+    b.close()
+    for m in members:
+        m.close()

@@ -107,3 +107,59 @@ def test_full_batch_members_after_burn_in_match_oracle():
     b.close()
     for m in members:
         m.close()
+
+
+def _block_reference(d, m, state, c, step0, dt, n_steps):
+    """Oracle counts of cell c after steps step0 .. step0 + n_steps - 1 of a
+    tissue too large for the whole oracle, from the GPU's state at step0: a
+    face carries influence one cell per phase along its axis, so simulating
+    the block of Chebyshev radius n_steps around c leaves c exact.  Returns
+    c's counts and its chi statistics of the last step."""
+    V, Wd, Hd = d.V, d.width, d.height
+    cx, cy = c % Wd, c // Wd
+    xs = [x for x in range(cx - n_steps, cx + n_steps + 1) if 0 <= x < Wd]
+    ys = [y for y in range(cy - n_steps, cy + n_steps + 1) if 0 <= y < Hd]
+    counts = np.zeros(d.cells * 3 * V, dtype=np.int32)
+    for y in ys:
+        for x in xs:
+            b = (y * Wd + x) * 3 * V
+            counts[b:b + 3 * V] = state[b:b + 3 * V]
+    stats = None
+    for k in range(step0, step0 + n_steps):
+        for y in ys:
+            for x in xs:
+                st = O.chi_cell(d, m, counts, y * Wd + x, k, dt)
+                if y * Wd + x == c:
+                    stats = st
+        for y in ys:
+            for x in xs[:-1]:
+                O.sig_face(d, m, counts, y * Wd + x, 0, k, dt)
+        for y in ys[:-1]:
+            for x in xs:
+                O.sig_face(d, m, counts, y * Wd + x, 1, k, dt)
+    return counts[c * 3 * V:(c + 1) * 3 * V].copy(), stats
+
+
+def test_large_tissue_after_burn_in_sampled_cells_match_oracle():
+    """256x256 cells of 32x32 voxels (16-bit counts in shared memory) after 2
+    time units, the state the benchmark's large leg times from; 2 more steps,
+    sampled cells (corners, edges, interior) checked against the oracle on
+    the neighbourhood that can influence them."""
+    run = W.large()
+    spec = run.tissue
+    d, m = orc_desc(spec), orc_model(spec)
+    g = Tissue(spec)  # default launch shape, as the benchmark uses
+    g.step(run.dt, 20)
+    state, k0 = g.read_counts(), g.get_step()
+    g.step(run.dt, 2)
+    got = g.read_counts()
+    gne, gtl = g.read_stats()
+    g.close()
+    Wd, V = spec.width, spec.V
+    rng = np.random.default_rng(101)
+    samples = [0, Wd - 1, Wd * (Wd - 1), Wd * Wd - 1, Wd * 100 + 3] + \
+              [int(x) for x in rng.integers(0, spec.cells, size=5)]
+    for c in samples:
+        ref, (ne, tl) = _block_reference(d, m, state, c, k0, run.dt, 2)
+        assert gne[0, c] == ne and _bits(gtl[0, c]) == _bits(tl), c
+        assert np.array_equal(got[c * 3 * V:(c + 1) * 3 * V], ref), c

@@ -41,6 +41,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -75,7 +76,7 @@ CHI_SOURCES = ["chi_seg.cuh", "tissue_dev.cuh", "tissue_internal.h", "k_chi_seg.
 # `sources` is chi_sources_sha() of the kernel they were measured on: when the
 # kernel changes, the figures are stale and the roofline reports none.
 CHI_IPE = {
-    "sources": "61e143ea42c52fb3",
+    "sources": "d535947580551bc1",
     "kernels": {
         "batch:V1024/H32/pre/qb0/nd/u16": (543.6, 0.6820),
         "batch:V256/H16/pre/qb0/nd/u32": (301.5, 0.4484),
@@ -92,13 +93,29 @@ CHI_IPE = {
 }
 
 
-def chi_sources_sha() -> str:
-    """SHA-256 over the persistent chi kernel's sources and the nvcc flags."""
+def _code_of(name: str, text: str) -> str:
+    """The part of a source file that fixes the kernel's instructions: the
+    text without comments or blank lines; of tissue_internal.h only the device
+    structures and constants before its host-side launcher declarations."""
+    if name == "tissue_internal.h":
+        text = text[:text.index("cudaError_t launch_")]
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln.strip())
+
+
+def chi_sources_sha(read=None) -> str:
+    """SHA-256 over the persistent chi kernel's code (comments stripped) and
+    the nvcc flags.  read(name) returns a source's text (default: the files
+    in csrc/)."""
     from paper_1806_10889_gb300.build import NVCC_FLAGS
+    if read is None:
+        def read(name):
+            with open(os.path.join(CSRC, name)) as fh:
+                return fh.read()
     h = hashlib.sha256()
     for f in CHI_SOURCES:
-        with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(f.encode() + b"\0" + fh.read())
+        h.update(f.encode() + b"\0" + _code_of(f, read(f)).encode())
     h.update(" ".join(x for x in NVCC_FLAGS if not x.startswith("-I")).encode())
     return h.hexdigest()[:16]
 

@@ -70,3 +70,16 @@ def test_serving_requests_cap_replicas_only():
         assert b.replicas == min(a.replicas, 2)
         assert (a.index, a.arrival_s, a.side, a.n, a.n_steps) == (b.index, b.arrival_s, b.side,
                                                                   b.n, b.n_steps)
+
+
+def test_kernel_hash_ignores_comments_but_not_code():
+    import os
+    base = {f: open(os.path.join(bench.CSRC, f)).read() for f in bench.CHI_SOURCES}
+    sha = bench.chi_sources_sha(base.get)
+    commented = dict(base, **{"chi_seg.cuh": "// a note\n" + base["chi_seg.cuh"] + "\n/* more */\n"})
+    assert bench.chi_sources_sha(commented.get) == sha
+    hosty = dict(base, **{"tissue_internal.h": base["tissue_internal.h"] + "\nint host_only(int);\n"})
+    assert bench.chi_sources_sha(hosty.get) == sha
+    changed = dict(base, **{"tissue_dev.cuh": base["tissue_dev.cuh"].replace(
+        "0xD2511F53u", "0xD2511F55u", 1)})
+    assert bench.chi_sources_sha(changed.get) != sha

@@ -430,18 +430,27 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        phases = np.zeros(3)  # host wall seconds: write, step (to its end), read
         t0 = time.perf_counter()
         for i in range(args.e2e_steps):
+            ta = time.perf_counter()
             bt.write_counts(hosts, step_index=k0 + i)  # H2D of every member's input state
+            tb = time.perf_counter()
             bt.step(dt, 1)
+            bt.sync()
+            tc = time.perf_counter()
             bt.read_counts(hosts)                      # D2H of every member's result
+            phases += (tb - ta, tc - tb, time.perf_counter() - tc)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         e_ev = float((_events(members) - e0).sum())
         e2e_s, e_ev = job_totals(dist, e2e_s, e_ev)
         nbytes = sum(r.tissue.state_ints * 4 for r in runs)
         e2e = {"value": e_ev / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
+               "ms_per_step": {"write": 1e3 * phases[0] / args.e2e_steps,
+                               "step": 1e3 * phases[1] / args.e2e_steps,
+                               "read": 1e3 * phases[2] / args.e2e_steps}}
 
     # plain per-tissue launches against the batch, from the same state
     plain = None

@@ -212,7 +212,7 @@ int tissue_set_launch(tissue* t, uint32_t chi_warps_per_block);
 #define TISSUE_KERNEL_WARP 0u       /* one warp per cell, one launch over all cells */
 #define TISSUE_KERNEL_PERSISTENT 1u /* persistent kernel, cells taken from a work list */
 #define TISSUE_LAYOUT_PREFIX 0u    /* persistent kernel keeps per-voxel prefix sums (20 B/voxel; 14 B with 16-bit counts, cells of V > 256) */
-#define TISSUE_LAYOUT_RECOMPUTE 1u /* counts only (12 B/voxel); <= 4 warps per block, V <= lanes^2 */
+#define TISSUE_LAYOUT_RECOMPUTE 1u /* counts only (12 B/voxel; 6 with 16-bit counts, cells of V > 256); <= 4 warps per block, V <= lanes^2 or, for the Notch-Delta model, 16 lanes and V <= 1024 or 8 lanes and V <= 256 */
 typedef struct {
   uint32_t kernel;          /* TISSUE_KERNEL_WARP or TISSUE_KERNEL_PERSISTENT */
   uint32_t lanes_per_cell;  /* persistent kernel: 32, 16 or 8 (1, 2 or 4 cells per warp) */
@@ -220,11 +220,16 @@ typedef struct {
   uint32_t blocks;          /* persistent kernel grid; 0 = enough to fill every SM */
   uint32_t smem_layout;     /* persistent kernel: TISSUE_LAYOUT_PREFIX or _RECOMPUTE */
 } tissue_launch;
-/* The default after tissue_create: persistent kernel, prefix layout; for a
- * tissue of at most 1024 cells 32 lanes and 2 warps per block (one cell per
+/* The default after tissue_create: persistent kernel; for a tissue of at
+ * most 1024 cells 32 lanes and 2 warps per block, prefix layout (one cell per
  * warp: the shortest event chain, which sets the time when the machine is
  * not full); otherwise by cell size, 8 lanes and 4 warps per block for
- * V <= 64, 16 lanes and 4 warps for V <= 256, 32 lanes and 2 warps above. */
+ * V <= 64, 16 lanes and 4 warps for V <= 256 (prefix layout), and above
+ * that 16 lanes, 2 warps per block and the recompute layout from 8192 cells
+ * (more cells resident per SM), else 32 lanes and 2 warps, prefix layout.
+ * A recompute launch with more voxels per block than lanes that the
+ * tissue's model cannot take (the promoter model, a trace) runs that last
+ * prefix launch instead; results never depend on it. */
 int tissue_set_launch_config(tissue* t, const tissue_launch* config);
 int tissue_get_launch_config(const tissue* t, tissue_launch* config);
 
@@ -248,7 +253,9 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
 
 /* Launch shape of the chi launch of the class of cells with V voxels:
  * 8, 16 or 32 lanes per cell, 1..8 warps per block (1..4 with the recompute
- * layout, which also needs V <= lanes^2), shared-memory layout TISSUE_LAYOUT_*.  The default is
+ * layout, which also needs V <= lanes^2, or for a Notch-Delta class 16 lanes
+ * and V <= 1024 or 8 lanes and V <= 256), shared-memory layout
+ * TISSUE_LAYOUT_*.  The default is
  * the single-tissue default for that V.  Results never depend on it. */
 int tissue_batch_set_class_launch(tissue_batch* b, uint32_t V, uint32_t lanes_per_cell,
                                   uint32_t warps_per_block, uint32_t smem_layout);

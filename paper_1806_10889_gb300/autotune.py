@@ -28,14 +28,22 @@ class VariantMismatch(RuntimeError):
     """Two launch variants produced different trajectories."""
 
 
+def _recompute_fits(V: int, lanes: int) -> bool:
+    """The counts-only layout takes cells of V voxels with this many lanes:
+    a block fits the lanes (V <= lanes^2), or the lanes cover up to four
+    voxels each (16 lanes and V <= 1024, 8 lanes and V <= 256; Notch-Delta
+    launches, others run the prefix layout)."""
+    return V <= lanes * lanes or (lanes == 16 and V <= 1024) or (lanes == 8 and V <= 256)
+
+
 def tissue_candidates(V: int) -> list[tuple]:
     """(kernel, lanes per cell, warps per block, blocks, shared-memory layout)
     candidates for cells of V voxels."""
     c = [(KERNEL_WARP, 32, w, 0, LAYOUT_PREFIX) for w in (2, 4, 8)]
     for lanes in (8, 16, 32):
         c += [(KERNEL_PERSISTENT, lanes, w, 0, LAYOUT_PREFIX) for w in (1, 2, 4)]
-        if V <= lanes * lanes:
-            c += [(KERNEL_PERSISTENT, lanes, w, 0, LAYOUT_RECOMPUTE) for w in (2, 4)]
+        if _recompute_fits(V, lanes):
+            c += [(KERNEL_PERSISTENT, lanes, w, 0, LAYOUT_RECOMPUTE) for w in (1, 2, 4)]
     return c
 
 
@@ -44,8 +52,8 @@ def batch_class_candidates(V: int) -> list[tuple]:
     c = []
     for lanes in (8, 16, 32):
         c += [(lanes, w, LAYOUT_PREFIX) for w in (1, 2, 4)]
-        if V <= lanes * lanes:
-            c += [(lanes, w, LAYOUT_RECOMPUTE) for w in (2, 4)]
+        if _recompute_fits(V, lanes):
+            c += [(lanes, w, LAYOUT_RECOMPUTE) for w in (1, 2, 4)]
     return c
 
 

@@ -74,18 +74,20 @@ __device__ __forceinline__ void voxel_terms(bool pm, const QRates& q, int v, con
   }
 }
 
-// Hill values held in registers: with one cell per warp (H = 32), lane j
-// keeps Hill(j), read from its tissue's table when the warp takes a cell.
-// Repressor counts per voxel are small (a few tens in a running tissue), so
-// most lookups of the event loop become register shuffles instead of table
-// loads on the event's dependency chain; larger counts fall back to the
-// table.  With 16 or 8 lanes the two extra registers cost more than they
-// save (a resident block per SM at 16 lanes; same-box A/B), so those
-// instantiations read the table (kSets = 0).  The code handles up to two
-// sets per lane (Hill(j) and Hill(j + H)).
-template <int H>
+// Hill values held in registers: lane j of a segment keeps Hill(j) (SETS = 1)
+// and Hill(j + H) (SETS = 2), read from its tissue's table when the segment
+// takes a cell.  Repressor counts per voxel are small (a few tens in a
+// running tissue), so most lookups of the event loop become register
+// shuffles instead of table loads on the event's dependency chain; larger
+// counts fall back to the table.  The kernel uses one set with one cell per
+// warp (H = 32) and in the counts-only layout, which looks up every voxel of
+// the selected block, one set at 16 lanes and two at 8 (R < 16); with the
+// prefix layout at 16 or 8 lanes the extra registers cost more than they
+// save (a resident block per SM at 16 lanes; same-box A/B), so those read
+// the table (SETS = 0).
+template <int H, int SETS>
 struct HillRegs {
-  static constexpr int kSets = H == 32 ? 1 : 0;
+  static constexpr int kSets = SETS;
   static constexpr uint32_t kCover = static_cast<uint32_t>(kSets * H);
   uint64_t h0 = 0, h1 = 0;
 
@@ -212,7 +214,7 @@ __device__ __forceinline__ uint64_t chan_cum(const ChanLane& c, const LaneK& k, 
 // items[0 .. n) are the work (n = *n_items_dev when that is given, else
 // n_items); NARROW appends the cells it gives up on to redo[*redo_n ...].
 template <int H, bool PRE, bool QB, int GEN, bool NARROW>
-__global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (NARROW ? 5 : 8)) k_chi_seg(
+__global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (QB ? 4 : (NARROW ? 5 : 8))) k_chi_seg(
                                                  const TissueView* __restrict__ views,
                                                  const uint2* __restrict__ items,
                                                  const uint32_t n_items, uint32_t* counter,
@@ -237,9 +239,11 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (NARROW ? 5 : 8)) k
   const ChanLane cl = chan_lane(sl);
   const ChanLane cl2 = chan_lane(sl + H);  // second channel of each lane when H = 8
   LaneK lk{}, lk2{};                         // their coefficients for the current cell
-  HillRegs<H> hreg;                          // Hill(R) of small R for the current cell
+  HillRegs<H, (!PRE && H == 8) ? 2 : (H == 32 || (!PRE && H == 16)) ? 1 : 0> hreg;
 
-  static_assert(PRE || !QB, "the recompute layout needs B <= H");
+  // The counts-only layout covers up to four voxels of a block per lane
+  // (B > H) with 16 lanes (V <= 1024) or 8 lanes (V <= 256).
+  static_assert(PRE || !QB || H == 16 || H == 8, "recompute layout with B > H: 8 or 16 lanes");
   bool have = false, done = false, pm = false;
   bool oob = false;  // checked build: an index out of range (see TSG_IDX)
   Seg s{0, 2, 1, 0, 1, 0, 0};
@@ -412,29 +416,40 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (NARROW ? 5 : 8)) k
     const int vb = L << s.lb;
     const QRates& q = sv->q;
     uint64_t pv = ~0ull;
+    uint64_t run[4] = {0ull, 0ull, 0ull, 0ull};  // counts-only layout: a lane's running sums
     if (PRE) {
       // lane sl covers voxels vb + sl*Q .. + Q-1 of the block (Q = 2^qb; 1 if B <= H)
       const int q0 = vb + (sl << qb);
       if ((sl << qb) < s.B && q0 < s.V)
         pv = pre[TSG_IDX(min(q0 + (1 << qb) - 1, s.V - 1), vmax, oob)];
     } else {
-      // the block's voxel propensities, recomputed, then their running sum
+      // the block's voxel propensities, recomputed: lane sl covers voxels
+      // vb + sl*Q .. + Q-1 (Q = 2^qb; Q = 1 unless QB), keeps their running
+      // sums in run[], and the lanes' totals are then scanned across the
+      // segment
+      constexpr int kQ = QB ? 4 : 1;
       bool unused = false;
-      const bool mine = act && sl < s.B && vb + sl < s.V;
-      const int bx = mine ? vb + sl : 0;
-      const int bi = static_cast<int>(TSG_IDX(bx, vmax, oob));
-      const uint32_t bD = static_cast<uint32_t>(cnt[bi]);
-      const uint32_t bN = static_cast<uint32_t>(cnt[vmax + bi]);
-      const uint32_t bR = static_cast<uint32_t>(cnt[2 * vmax + bi]);
-      const uint64_t bh = GEN == 2 ? 0ull : hreg.get(q, bR, mine && !PM);
-      uint64_t cx =
-          mine ? voxel_total_of<(GEN != 0)>(bx, bD, bN, bR, bh, s, q, PM, unused) : 0ull;
+      uint64_t acc = 0ull;
+#pragma unroll
+      for (int k = 0; k < kQ; ++k) {
+        const int off = (sl << qb) + k;
+        const bool mine = act && k < (1 << qb) && off < s.B && vb + off < s.V;
+        const int bx = mine ? vb + off : 0;
+        const int bi = static_cast<int>(TSG_IDX(bx, vmax, oob));
+        const uint32_t bD = static_cast<uint32_t>(cnt[bi]);
+        const uint32_t bN = static_cast<uint32_t>(cnt[vmax + bi]);
+        const uint32_t bR = static_cast<uint32_t>(cnt[2 * vmax + bi]);
+        const uint64_t bh = GEN == 2 ? 0ull : hreg.get(q, bR, mine && !PM);
+        acc += mine ? voxel_total_of<(GEN != 0)>(bx, bD, bN, bR, bh, s, q, PM, unused) : 0ull;
+        run[k] = acc;
+      }
+      uint64_t cx = acc;
 #pragma unroll
       for (int o = 1; o < H; o <<= 1) {
         const uint64_t y = __shfl_up_sync(kFull, cx, o, H);
         if (sl >= o) cx += y;
       }
-      if (sl < s.B && vb + sl < s.V) pv = cx;
+      if ((sl << qb) < s.B && vb + (sl << qb) < s.V) pv = cx;
     }
     const unsigned m2 = (__ballot_sync(kFull, r1 < pv) >> (seg * H)) & kSegBits;
     const int i2 = m2 ? __ffs(m2) - 1 : 0;
@@ -442,6 +457,26 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (NARROW ? 5 : 8)) k
     uint64_t r2 = r1 - (i2 > 0 ? pp : 0ull);
     int v = vb + (i2 << qb);
     bool bad_q = false;
+    if (!PRE && QB) {
+      // the voxel inside lane i2's run of Q = 2^qb voxels: every lane finds
+      // the first of its own running sums above r2, and lane i2's answer is
+      // taken (an empty run of zero-propensity voxels is never chosen)
+      int kq = -1;
+      uint64_t below = 0ull;
+#pragma unroll
+      for (int k = 3; k >= 0; --k)
+        if (k < (1 << qb) && r2 < run[k]) {
+          kq = k;
+          below = k > 0 ? run[k > 0 ? k - 1 : 0] : 0ull;
+        }
+      const int ks = __shfl_sync(kFull, kq, i2, H);
+      const uint64_t bs = __shfl_sync(kFull, below, i2, H);
+      bad_q = ks < 0;
+      if (ks >= 0) {
+        v += ks;
+        r2 -= bs;
+      }
+    }
     if (PRE && QB) {
       // the voxel inside lane i2's run of Q = 2^qb voxels: the segment's
       // lanes read H of the run's prefix entries at a time and one ballot
@@ -543,13 +578,17 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (NARROW ? 5 : 8)) k
     if (PRE) {
       // lane 0 the new total of v, lane 1 that of u (the hop's target)
       const int xv = (sl == 1 && u >= 0) ? u : v;
-      const int xi = static_cast<int>(TSG_IDX(xv, vmax, oob));
-      const uint32_t xD = static_cast<uint32_t>(cnt[xi]);
-      const uint32_t xN = static_cast<uint32_t>(cnt[vmax + xi]);
-      const uint32_t xR = static_cast<uint32_t>(cnt[2 * vmax + xi]);
-      const uint64_t xh = GEN == 2 ? 0ull : hreg.get(q, xR, act && !PM);
-      const uint64_t a_new =
-          act ? voxel_total_of<(GEN != 0)>(xv, xD, xN, xR, xh, s, q, PM, ovf) : 0ull;
+      uint64_t a_new;
+      if (decltype(hreg)::kSets == 0) {  // table lookups, inside the active branch
+        a_new = act ? seg_voxel_total<(GEN != 0)>(cnt, vmax, xv, s, q, PM, ovf, oob) : 0ull;
+      } else {  // register lookups: every lane takes part in the shuffles
+        const int xi = static_cast<int>(TSG_IDX(xv, vmax, oob));
+        const uint32_t xD = static_cast<uint32_t>(cnt[xi]);
+        const uint32_t xN = static_cast<uint32_t>(cnt[vmax + xi]);
+        const uint32_t xR = static_cast<uint32_t>(cnt[2 * vmax + xi]);
+        const uint64_t xh = GEN == 2 ? 0ull : hreg.get(q, xR, act && !PM);
+        a_new = act ? voxel_total_of<(GEN != 0)>(xv, xD, xN, xR, xh, s, q, PM, ovf) : 0ull;
+      }
       dv = __shfl_sync(kFull, a_new, 0, H) - a_old_v;
       du = __shfl_sync(kFull, a_new, 1, H) - a_old_u;
     } else {

@@ -10,11 +10,12 @@ namespace {
 template <int GEN>
 ChiSegKernel pick(int H, bool pre, bool qb) {
   if (H == 8) {
-    if (!pre) return k_chi_seg<8, false, false, GEN, false>;
+    if (!pre) return qb ? k_chi_seg<8, false, true, GEN, false> : k_chi_seg<8, false, false, GEN, false>;
     return qb ? k_chi_seg<8, true, true, GEN, false> : k_chi_seg<8, true, false, GEN, false>;
   }
   if (H == 16) {
-    if (!pre) return k_chi_seg<16, false, false, GEN, false>;
+    // the counts-only layout with several voxels per lane: Notch-Delta only
+    if (!pre) return qb ? k_chi_seg<16, false, true, GEN, false> : k_chi_seg<16, false, false, GEN, false>;
     return qb ? k_chi_seg<16, true, true, GEN, false> : k_chi_seg<16, true, false, GEN, false>;
   }
   if (!pre) return k_chi_seg<32, false, false, GEN, false>;
@@ -24,6 +25,11 @@ ChiSegKernel pick(int H, bool pre, bool qb) {
 }  // namespace
 
 ChiSegKernel chi_seg_kernel_nd(int H, bool pre, bool qb) { return pick<0>(H, pre, qb); }
+
+bool recompute_covers(uint32_t V, int H, int gen) {
+  return V <= static_cast<uint32_t>(H * H) ||
+         (gen == 0 && ((H == 16 && V <= 1024) || (H == 8 && V <= 256)));
+}
 
 int seg_lanes_for(uint32_t V, int want) {
   if (want == 16 && V <= 256) return 16;
@@ -79,10 +85,11 @@ cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint
   if (H != 8 && H != 16 && H != 32) return cudaErrorInvalidValue;
   if (!pre && warps_per_block > 4) return cudaErrorInvalidValue;
   // B > H (a lane covers several voxels of a block) only when V > H^2; the
-  // recompute layout requires V <= H^2.
+  // recompute layout allows that only for the Notch-Delta model, up to four
+  // voxels per lane (16 lanes and V <= 1024, or 8 lanes and V <= 256).
   const bool qb = vmax_cells > static_cast<uint32_t>(H * H);
-  if (!pre && qb) return cudaErrorInvalidValue;
   if (gen < 0 || gen > 2) return cudaErrorInvalidValue;
+  if (!pre && qb && !recompute_covers(vmax_cells, H, gen)) return cudaErrorInvalidValue;
   const ChiSegKernel k = gen == 2   ? chi_seg_kernel_pm(H, pre, qb)
                          : gen == 1 ? chi_seg_kernel_gen(H, pre, qb)
                                     : chi_seg_kernel_nd(H, pre, qb);

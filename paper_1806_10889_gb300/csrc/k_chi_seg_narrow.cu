@@ -8,8 +8,12 @@ namespace tsg {
 
 ChiSegKernel chi_seg_kernel_narrow(int H, bool pre, bool qb) {
   // V > 256 makes B > H for 8 and 16 lanes; 32 lanes cover V <= 1024 with B <= H.
-  // The recompute layout needs B <= H: 32 lanes only.
-  if (!pre) return (H == 32 && !qb) ? k_chi_seg<32, false, false, 0, true> : nullptr;
+  // The recompute layout: 32 lanes, or 16 lanes with up to four voxels per lane.
+  if (!pre) {
+    if (H == 32) return qb ? nullptr : k_chi_seg<32, false, false, 0, true>;
+    if (H == 16) return qb ? k_chi_seg<16, false, true, 0, true> : nullptr;
+    return nullptr;
+  }
   if (H == 8) return qb ? k_chi_seg<8, true, true, 0, true> : nullptr;
   if (H == 16) return qb ? k_chi_seg<16, true, true, 0, true> : nullptr;
   return qb ? nullptr : k_chi_seg<32, true, false, 0, true>;

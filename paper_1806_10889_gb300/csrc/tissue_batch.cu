@@ -82,9 +82,17 @@ int chi_all(tissue_batch* b, double dt) {
     if (cudaMemsetAsync(counters, 0, 3 * sizeof(uint32_t), b->stream) != cudaSuccess)
       return TISSUE_E_CUDA;
     const ChiRedo redo{b->d_redo, counters};
+    // as for single tissues: a counts-only launch with several voxels per
+    // lane takes Notch-Delta classes without a trace; others run the prefix
+    // launch of the class (the same trajectories)
+    tissue_launch lc{TISSUE_KERNEL_PERSISTENT, p.lanes, p.warps_per_block, 0, p.layout};
+    if (lc.smem_layout == TISSUE_LAYOUT_RECOMPUTE &&
+        !recompute_covers(p.V, static_cast<int>(p.lanes), p.gen))
+      lc = prefix_launch(p.V, p.n_items);
     if (launch_chi_seg(b->d_views, b->d_items + p.items_off, p.n_items, counters, p.V,
-                       static_cast<int>(p.lanes), static_cast<int>(p.warps_per_block), 0, 0u, dt,
-                       p.layout == TISSUE_LAYOUT_PREFIX, p.gen, &redo, b->stream) != cudaSuccess)
+                       static_cast<int>(lc.lanes_per_cell), static_cast<int>(lc.warps_per_block),
+                       0, 0u, dt, lc.smem_layout == TISSUE_LAYOUT_PREFIX, p.gen, &redo,
+                       b->stream) != cudaSuccess)
       return TISSUE_E_CUDA;
     if (mark(b, 4 + c) != TISSUE_OK) return TISSUE_E_CUDA;
   }
@@ -251,7 +259,8 @@ int tissue_batch_set_class_launch(tissue_batch* b, uint32_t V, uint32_t lanes_pe
   if (lanes_per_cell != 8 && lanes_per_cell != 16 && lanes_per_cell != 32) return TISSUE_E_ARG;
   if (smem_layout != TISSUE_LAYOUT_PREFIX && smem_layout != TISSUE_LAYOUT_RECOMPUTE)
     return TISSUE_E_ARG;
-  if (smem_layout == TISSUE_LAYOUT_RECOMPUTE && V > lanes_per_cell * lanes_per_cell)
+  if (smem_layout == TISSUE_LAYOUT_RECOMPUTE &&
+      !recompute_covers(V, static_cast<int>(lanes_per_cell), 0))
     return TISSUE_E_ARG;
   const bool pre = smem_layout == TISSUE_LAYOUT_PREFIX;
   if (warps_per_block < 1 || warps_per_block > (pre ? 8u : 4u)) return TISSUE_E_ARG;

@@ -131,6 +131,10 @@ ChiSegKernel chi_seg_kernel_pm(int H, bool pre, bool qb);   // k_chi_seg_pm.cu
 // counts-only layout at 32 lanes); nullptr where not built.
 ChiSegKernel chi_seg_kernel_narrow(int H, bool pre, bool qb);  // k_chi_seg_narrow.cu
 uint32_t seg_bytes_for(uint32_t V, int H, bool pre, bool narrow = false);
+// Whether the counts-only (recompute) layout takes cells of V voxels with H
+// lanes for launches of model code gen (k_chi_seg.cu): V <= H^2, or for the
+// Notch-Delta model (gen 0) up to four voxels per lane.
+bool recompute_covers(uint32_t V, int H, int gen);
 // Well-mixed cells (k_chi_wm.cu): one warp per (tissue, cell) item;
 // vmax_cells is the largest V among the listed cells.
 cudaError_t launch_chi_wm(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
@@ -158,7 +162,13 @@ struct TissueInfo {
 bool tissue_info(const tissue* t, TissueInfo* out);
 // The default chi launch for `cells` cells of V voxels (one launch).
 constexpr uint64_t kFewCells = 1024;
+// From this many cells of more than 256 voxels the default launch takes the
+// counts-only layout with 16 lanes (about two waves of its 4,864 cells).
+constexpr uint64_t kManyCells = 8192;
 tissue_launch default_launch(uint32_t V, uint64_t cells);
+// The default among prefix-layout launches (the fallback of a counts-only
+// launch that cannot take a tissue's model).
+tissue_launch prefix_launch(uint32_t V, uint64_t cells);
 void tissue_advance_host_step(tissue* t, uint32_t n);
 void tissue_set_host_step(tissue* t, uint32_t step_index);
 // A latched device error flag as the C ABI's status code.

@@ -142,7 +142,7 @@ cudaError_t tsg::lib_malloc(void** p, size_t bytes) {
   return cudaMalloc(p, bytes);
 }
 
-tissue_launch tsg::default_launch(uint32_t V, uint64_t cells) {
+tissue_launch tsg::prefix_launch(uint32_t V, uint64_t cells) {
   // Up to ~1,000 cells the machine is not full and each cell's event chain
   // sets the time: one cell per warp has the shortest chain (measured:
   // 2,790 against 2,930 and 3,220 SM cycles per event with 16 and 8 lanes on
@@ -155,13 +155,33 @@ tissue_launch tsg::default_launch(uint32_t V, uint64_t cells) {
   return tissue_launch{TISSUE_KERNEL_PERSISTENT, 32, 2, 0, TISSUE_LAYOUT_PREFIX};
 }
 
+tissue_launch tsg::default_launch(uint32_t V, uint64_t cells) {
+  // Cells of more than 256 voxels in launches of many waves: two cells per
+  // warp in the counts-only layout (16-bit counts, 6.4 KB per cell: 32 cells
+  // per SM against 14 with the prefix layout) recomputing the selected block,
+  // four voxels per lane.  Same-box A/B, 256x256 cells of 32x32 voxels: 876
+  // -> 710 ms per chi step.  Fewer cells than about two waves of it keep one
+  // cell per warp, whose event chain is shorter.  Launches the counts-only
+  // layout cannot take (the promoter model, a trace) run prefix_launch.
+  if (V > 256 && V <= 1024 && cells >= kManyCells)
+    return tissue_launch{TISSUE_KERNEL_PERSISTENT, 16, 2, 0, TISSUE_LAYOUT_RECOMPUTE};
+  return prefix_launch(V, cells);
+}
+
 namespace {
 
 // chi for step offset i, in the tissue's launch configuration.
 cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt) {
-  const tissue_launch& c = t->cfg;
+  tissue_launch c = t->cfg;
   if (c.kernel == TISSUE_KERNEL_PERSISTENT) {
     const uint32_t cells = t->d.width * t->d.height;
+    const int gen = t->q.kind == kModelPromoter ? 2 : t->d_trace != nullptr ? 1 : 0;
+    // A counts-only launch with several voxels per lane runs Notch-Delta
+    // launches without a trace only; others take the prefix launch of the
+    // cell size (the same trajectory, bit for bit).
+    if (c.smem_layout == TISSUE_LAYOUT_RECOMPUTE &&
+        !recompute_covers(v.V, static_cast<int>(c.lanes_per_cell), gen))
+      c = prefix_launch(v.V, cells - t->wm_cells);
     cudaError_t e = cudaSuccess;
     if (t->wm_cells) {  // well-mixed cells first, then the lattice cells by list
       e = launch_chi_wm(t->d_view, t->d_wm_items, t->wm_cells, v.V, i, dt, t->stream);
@@ -170,12 +190,11 @@ cudaError_t launch_chi_cfg(tissue* t, const TissueView& v, uint32_t i, double dt
     e = cudaMemsetAsync(t->d_work, 0, 3 * sizeof(uint32_t), t->stream);
     if (e != cudaSuccess) return e;
     const ChiRedo redo{t->d_redo, t->d_work};
+    const bool pre = c.smem_layout == TISSUE_LAYOUT_PREFIX;
     return launch_chi_seg(t->d_view, t->wm_cells ? t->d_lat_items : nullptr, cells - t->wm_cells,
                           t->d_work, v.V, static_cast<int>(c.lanes_per_cell),
                           static_cast<int>(c.warps_per_block), static_cast<int>(c.blocks), i, dt,
-                          c.smem_layout == TISSUE_LAYOUT_PREFIX,
-                          t->q.kind == kModelPromoter ? 2 : t->d_trace != nullptr ? 1 : 0, &redo,
-                          t->stream);
+                          pre, gen, &redo, t->stream);
   }
   return launch_chi(v, i, dt, static_cast<int>(c.warps_per_block), t->stream);
 }
@@ -576,8 +595,10 @@ int tissue_set_launch_config(tissue* t, const tissue_launch* c) {
   } else if (c->kernel == TISSUE_KERNEL_PERSISTENT) {
     if (c->lanes_per_cell != 32 && c->lanes_per_cell != 16 && c->lanes_per_cell != 8)
       return TISSUE_E_ARG;
-    // the recompute layout needs a block to fit the segment's lanes (V <= lanes^2)
-    if (c->smem_layout == TISSUE_LAYOUT_RECOMPUTE && V > c->lanes_per_cell * c->lanes_per_cell)
+    // the recompute layout needs a block to fit the segment's lanes
+    // (V <= lanes^2), or 16 lanes and V <= 1024 for the Notch-Delta model
+    if (c->smem_layout == TISSUE_LAYOUT_RECOMPUTE &&
+        !recompute_covers(V, static_cast<int>(c->lanes_per_cell), 0))
       return TISSUE_E_ARG;
     if (c->smem_layout != TISSUE_LAYOUT_PREFIX && c->smem_layout != TISSUE_LAYOUT_RECOMPUTE)
       return TISSUE_E_ARG;

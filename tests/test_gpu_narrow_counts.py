@@ -72,9 +72,10 @@ def _run(spec, x0, dt, n_steps, config=None):
 
 
 @pytest.mark.parametrize("n", [32, 20, 21])  # 21: V = 441, not a multiple of 4 (scalar copies)
-def test_counts_above_16_bits_are_redone_bit_exact(n):
+@pytest.mark.parametrize("config", [None, (P, 16, 2, 0, REC)])  # 16 lanes, counts only: 2-4 voxels per lane
+def test_counts_above_16_bits_are_redone_bit_exact(n, config):
     spec = TissueSpec(3, 2, n, seed=71, tissue_id=3).with_model(**RELEASE)
-    ref, crossed = _run(spec, _big_state(spec), 0.05, 3)
+    ref, crossed = _run(spec, _big_state(spec), 0.05, 3, config)
     assert crossed, "cell 4 never passed 65535: the mid-step hand-back was not covered"
     x = ref.reshape(spec.cells, 3, spec.V)
     assert x[1, 0, 0] > LIMIT
@@ -82,7 +83,8 @@ def test_counts_above_16_bits_are_redone_bit_exact(n):
 
 @pytest.mark.parametrize("config", [(P, 32, 2, 0, PRE), (P, 32, 1, 3, PRE), (P, 16, 4, 0, PRE),
                                     (P, 16, 1, 1, PRE), (P, 8, 2, 0, PRE), (P, 8, 1, 0, PRE),
-                                    (P, 32, 2, 0, REC), (P, 32, 4, 0, REC), (P, 32, 1, 3, REC)])
+                                    (P, 32, 2, 0, REC), (P, 32, 4, 0, REC), (P, 32, 1, 3, REC),
+                                    (P, 16, 2, 0, REC), (P, 16, 1, 0, REC), (P, 16, 4, 5, REC)])
 def test_every_launch_shape_with_16_bit_counts(config):
     spec = TissueSpec(3, 2, 32, seed=73, tissue_id=1).with_model(**RELEASE)
     _, crossed = _run(spec, _big_state(spec), 0.05, 2, config)
@@ -104,9 +106,12 @@ def test_batch_shares_the_redo_list_across_classes():
         t.write_counts(x, 0)
     b = Batch(members)
     dt = 0.05
-    for k in range(4):
-        if k == 2:  # then the large-cell class with the counts-only layout
+    for k in range(6):
+        if k == 2:  # then the large-cell classes with the counts-only layout
             b.set_class_launch(1024, 32, 2, REC)
+        if k == 4:  # and with 16 lanes, several voxels per lane
+            b.set_class_launch(1024, 16, 2, REC)
+            b.set_class_launch(400, 16, 1, REC)
         b.step(dt, 1)
         b.sync()
         for i, s in enumerate(specs):

@@ -116,8 +116,9 @@ PERSISTENT = [(T.KERNEL_PERSISTENT, 32, 4, 0, T.LAYOUT_PREFIX),
 def test_persistent_kernel_matches_oracle(config, w, h, n, dt):
     """The persistent work-list kernel, one, two or four cells per warp, any
     grid (down to a single block pulling every cell), gives the oracle's bits."""
-    if config[4] == T.LAYOUT_RECOMPUTE and n * n > config[1] ** 2:
-        pytest.skip("the recompute layout needs V <= lanes^2")
+    if config[4] == T.LAYOUT_RECOMPUTE and n * n > config[1] ** 2 and \
+            not (config[1] == 16 and n * n <= 1024) and not (config[1] == 8 and n * n <= 256):
+        pytest.skip("the recompute layout needs V <= lanes^2, or 4 voxels per lane at most")
     lanes, wpb = config[1], config[2]
     blocks_v = 1
     while lanes * blocks_v < n * n:
@@ -131,8 +132,10 @@ def test_persistent_kernel_matches_oracle(config, w, h, n, dt):
 
 def test_launch_config_validation():
     g = Tissue(TissueSpec(2, 2, 32, seed=1))
-    with pytest.raises(T.TissueError):  # recompute layout: V = 1024 > 16^2
-        g.set_launch_config(T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE)
+    with pytest.raises(T.TissueError):  # recompute layout: V = 1024 is 16 voxels per lane at 8 lanes
+        g.set_launch_config(T.KERNEL_PERSISTENT, 8, 4, 0, T.LAYOUT_RECOMPUTE)
+    # 16 lanes cover up to four voxels each in the recompute layout (V <= 1024)
+    g.set_launch_config(T.KERNEL_PERSISTENT, 16, 4, 0, T.LAYOUT_RECOMPUTE)
     with pytest.raises(T.TissueError):
         g.set_launch_config(7, 32, 4, 0)
     with pytest.raises(T.TissueError):
@@ -363,3 +366,15 @@ def test_tiny_step_length():
     """dt = 1e-9: almost every call ends before its first event."""
     run = W.tiny()
     _run_both(run.tissue, 1e-9, 3)
+
+
+@pytest.mark.parametrize("lanes,n", [(16, 32), (16, 24), (16, 20), (16, 17), (8, 16), (8, 12),
+                                     (8, 9)])
+@pytest.mark.parametrize("wpb", [1, 2, 4])
+def test_counts_only_layout_with_several_voxels_per_lane(lanes, n, wpb):
+    """The counts-only layout with more voxels per block than lanes: every
+    lane recomputes 2 or 4 voxels of the selected block (16 lanes: V = 1024,
+    576, 400, 289; 8 lanes: V = 256, 144, 81; all but the first of each with
+    partly empty blocks), every step bit-exact with the oracle."""
+    spec = TissueSpec(3, 3, n, seed=300 + n, tissue_id=wpb).with_model(**STRONG)
+    _run_both(spec, 0.1, 3, config=(T.KERNEL_PERSISTENT, lanes, wpb, 0, T.LAYOUT_RECOMPUTE))

@@ -27,8 +27,9 @@ def _bits(x):
 @pytest.mark.parametrize("w,h,n,dt", [(4, 3, 8, 0.2), (3, 3, 16, 0.1), (2, 2, 32, 0.05),
                                       (5, 1, 6, 0.5)])
 def test_strang_matches_oracle(config, w, h, n, dt):
-    if config and config[4] == T.LAYOUT_RECOMPUTE and n * n > config[1] ** 2:
-        pytest.skip("the recompute layout needs V <= lanes^2")
+    if config and config[4] == T.LAYOUT_RECOMPUTE and n * n > config[1] ** 2 and \
+            not (config[1] == 16 and n * n <= 1024) and not (config[1] == 8 and n * n <= 256):
+        pytest.skip("the recompute layout needs V <= lanes^2, or 4 voxels per lane at most")
     spec = TissueSpec(w, h, n, seed=500 + n, tissue_id=7).with_model(k_bind=0.05)
     d, m = orc_desc(spec), orc_model(spec)
     ref = O.init_counts(d)

@@ -434,7 +434,7 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        phases = np.zeros(3)  # host wall seconds: write, step (to its end), read
+        phases = np.zeros((args.e2e_steps, 3))  # host wall s: write, step (to its end), read
         t0 = time.perf_counter()
         for i in range(args.e2e_steps):
             ta = time.perf_counter()
@@ -444,7 +444,7 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
             bt.sync()
             tc = time.perf_counter()
             bt.read_counts(hosts)                      # D2H of every member's result
-            phases += (tb - ta, tc - tb, time.perf_counter() - tc)
+            phases[i] = (tb - ta, tc - tb, time.perf_counter() - tc)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         e_ev = float((_events(members) - e0).sum())
@@ -452,9 +452,9 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
         nbytes = sum(r.tissue.state_ints * 4 for r in runs)
         e2e = {"value": e_ev / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
-               "ms_per_step": {"write": 1e3 * phases[0] / args.e2e_steps,
-                               "step": 1e3 * phases[1] / args.e2e_steps,
-                               "read": 1e3 * phases[2] / args.e2e_steps}}
+               "ms_per_step": {"write": [round(1e3 * x, 2) for x in phases[:, 0]],
+                               "step": [round(1e3 * x, 2) for x in phases[:, 1]],
+                               "read": [round(1e3 * x, 2) for x in phases[:, 2]]}}
 
     # plain per-tissue launches against the batch, from the same state
     plain = None

@@ -46,6 +46,10 @@ struct tissue_batch {
   uint32_t* d_io_steps = nullptr;  // checkpoint writes: the members' new step indices
   int* d_io_err = nullptr;         // checkpoint reads: the members' error flags
   int* d_io_bad = nullptr;         // checkpoint writes: a count out of range
+  // pinned host staging of the state I/O's small copies (step indices in,
+  // error flags out), so none of them goes through pageable memory
+  uint32_t* h_io_steps = nullptr;  // count entries
+  int* h_io_flags = nullptr;       // count error flags, then the range flag
   size_t xface_off = 0, yface_off = 0, wm_off = 0;
   uint32_t n_xfaces = 0, n_yfaces = 0;
   uint32_t n_wm = 0, wm_vmax = 0;  // well-mixed cells of all members (one launch)
@@ -231,24 +235,34 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
   b->d_io_steps = reinterpret_cast<uint32_t*>(io);
   b->d_io_err = reinterpret_cast<int*>(io + sizeof(uint32_t) * count);
   b->d_io_bad = reinterpret_cast<int*>(io + io_bytes);
+  if (cudaMallocHost(reinterpret_cast<void**>(&b->h_io_steps), sizeof(uint32_t) * count) !=
+          cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&b->h_io_flags), sizeof(int) * (count + 1)) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    if (b->h_io_steps) cudaFreeHost(b->h_io_steps);
+    cudaFree(b->dmem);
+    delete b;
+    return TISSUE_E_NOMEM;
+  }
   std::vector<TissueView> views(count);
   for (uint32_t i = 0; i < count; ++i) views[i] = info[i].view;
   // Members' pending work (creation, earlier steps) must finish before the
   // batch stream uses their buffers.
-  for (uint32_t i = 0; i < count; ++i)
-    if (cudaStreamSynchronize(info[i].stream) != cudaSuccess) {
-      cudaFree(b->dmem);
-      delete b;
-      return TISSUE_E_CUDA;
-    }
-  if (cudaMemcpy(b->d_views, views.data(), sizeof(TissueView) * count, cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      cudaMemcpy(b->d_items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice) !=
-          cudaSuccess) {
+  auto fail = [b]() {
+    cudaFreeHost(b->h_io_steps);
+    cudaFreeHost(b->h_io_flags);
     cudaFree(b->dmem);
     delete b;
     return TISSUE_E_CUDA;
-  }
+  };
+  for (uint32_t i = 0; i < count; ++i)
+    if (cudaStreamSynchronize(info[i].stream) != cudaSuccess) return fail();
+  if (cudaMemcpy(b->d_views, views.data(), sizeof(TissueView) * count, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(b->d_items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return fail();
   *out = b;
   return TISSUE_OK;
 }
@@ -363,19 +377,24 @@ int tissue_batch_write_counts(tissue_batch* b, const int32_t* const* host,
                         cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
       return TISSUE_E_CUDA;
   }
-  if (step_index && cudaMemcpyAsync(b->d_io_steps, step_index, sizeof(uint32_t) * n,
-                                    cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
-    return TISSUE_E_CUDA;
+  if (step_index) {
+    // the previous call's copies out of the staging area are complete: every
+    // call ends with a wait on the batch stream
+    std::copy(step_index, step_index + n, b->h_io_steps);
+    if (cudaMemcpyAsync(b->d_io_steps, b->h_io_steps, sizeof(uint32_t) * n,
+                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+      return TISSUE_E_CUDA;
+  }
   if (cudaMemsetAsync(b->d_io_bad, 0, sizeof(int), b->stream) != cudaSuccess ||
       launch_set_steps_list(b->d_views, step_index ? b->d_io_steps : nullptr, n, b->stream) !=
           cudaSuccess ||
       launch_check_counts_list(b->d_views, n, b->d_io_bad, b->stream) != cudaSuccess)
     return TISSUE_E_CUDA;
-  int bad = 0;
-  if (cudaMemcpyAsync(&bad, b->d_io_bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream) !=
-          cudaSuccess ||
+  if (cudaMemcpyAsync(b->h_io_flags + n, b->d_io_bad, sizeof(int), cudaMemcpyDeviceToHost,
+                      b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return TISSUE_E_CUDA;
+  const int bad = b->h_io_flags[n];
   if (step_index)
     for (uint32_t i = 0; i < n; ++i) tissue_set_host_step(b->members[i], step_index[i]);
   return bad ? TISSUE_E_ARG : TISSUE_OK;
@@ -396,13 +415,12 @@ int tissue_batch_read_counts(tissue_batch* b, int32_t* const* host) {
   }
   if (launch_gather_err_list(b->d_views, n, b->d_io_err, b->stream) != cudaSuccess)
     return TISSUE_E_CUDA;
-  std::vector<int> err(n);
-  if (cudaMemcpyAsync(err.data(), b->d_io_err, sizeof(int) * n, cudaMemcpyDeviceToHost,
+  if (cudaMemcpyAsync(b->h_io_flags, b->d_io_err, sizeof(int) * n, cudaMemcpyDeviceToHost,
                       b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return TISSUE_E_CUDA;
-  for (int e : err)
-    if (e) return error_code_of(e);
+  for (uint32_t i = 0; i < n; ++i)
+    if (b->h_io_flags[i]) return error_code_of(b->h_io_flags[i]);
   return TISSUE_OK;
 }
 
@@ -481,6 +499,8 @@ void tissue_batch_destroy(tissue_batch* b) {
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
   drop_events(b);
+  cudaFreeHost(b->h_io_steps);
+  cudaFreeHost(b->h_io_flags);
   cudaFree(b->dmem);
   delete b;
 }

@@ -68,7 +68,7 @@ CSRC = os.path.join(ROOT, "paper_1806_10889_gb300", "csrc")
 # The files that fix the persistent chi kernel's instruction stream.
 CHI_SOURCES = ["chi_seg.cuh", "tissue_dev.cuh", "tissue_internal.h", "k_chi_seg.cu",
                "k_chi_seg_narrow.cu", "k_chi_seg_gen.cu", "k_chi_seg_pm.cu"]
-# Warp instructions per chi event and DRAM bytes per launch of each
+# Warp instructions and DRAM bytes per chi event of each
 # instantiation of the persistent chi kernel (lanes per cell, layout, QB, model
 # code, 16-bit counts), measured by ncu (smsp__inst_executed.sum and
 # dram__bytes_{read,write}.sum over the chi launches of the command in
@@ -76,23 +76,23 @@ CHI_SOURCES = ["chi_seg.cuh", "tissue_dev.cuh", "tissue_internal.h", "k_chi_seg.
 # `sources` is chi_sources_sha() of the kernel they were measured on: when the
 # kernel changes, the figures are stale and the roofline reports none.
 CHI_IPE = {
-    "sources": "af1c35c12d4b97d7",
+    "sources": "dba69b5421b7d754",
     "kernels": {
-        "batch:V1024/H16/rec/qb1/nd/u16": (479.0, 0.6833),
-        "batch:V256/H16/pre/qb0/nd/u32": (302.6, 0.4483),
-        "batch:V64/H8/pre/qb0/nd/u32": (170.7, 0.5282),
-        "medium:V256/H16/pre/qb0/nd/u32": (297.5, 0.3086),
-        "large:V1024/H16/rec/qb1/nd/u16": (461.7, 1.3107),
+        "batch:V1024/H16/rec/qb1/nd/u16": (478.9, 0.6846),
+        "batch:V256/H16/pre/qb0/nd/u32": (302.2, 0.4487),
+        "batch:V64/H8/pre/qb0/nd/u32": (170.7, 0.5321),
+        "medium:V256/H16/pre/qb0/nd/u32": (297.5, 0.3094),
+        "large:V1024/H16/rec/qb1/nd/u16": (461.7, 1.3094),
         # launch shapes the autotuner may pick for the batch classes
-        "batch:V1024/H32/pre/qb0/nd/u16": (543.6, 0.6783),
-        "batch:V1024/H16/pre/qb1/nd/u16": (361.1, 0.6845),
-        "batch:V1024/H32/rec/qb0/nd/u16": (629.6, 0.6822),
-        "batch:V256/H8/pre/qb1/nd/u32": (207.3, 0.4532),
-        "batch:V256/H8/rec/qb1/nd/u32": (270.3, 0.4522),
-        "batch:V256/H32/pre/qb0/nd/u32": (551.6, 0.4484),
-        "batch:V64/H16/pre/qb0/nd/u32": (305.7, 0.5340),
-        "batch:V64/H32/pre/qb0/nd/u32": (551.9, 0.5364),
-        "batch:V64/H8/rec/qb0/nd/u32": (239.3, 0.5511),
+        "batch:V1024/H32/pre/qb0/nd/u16": (543.6, 0.6781),
+        "batch:V1024/H16/pre/qb1/nd/u16": (361.1, 0.6806),
+        "batch:V1024/H32/rec/qb0/nd/u16": (629.6, 0.6821),
+        "batch:V256/H8/pre/qb1/nd/u32": (207.0, 0.448),
+        "batch:V256/H8/rec/qb1/nd/u32": (270.9, 0.4512),
+        "batch:V256/H32/pre/qb0/nd/u32": (551.6, 0.4496),
+        "batch:V64/H16/pre/qb0/nd/u32": (305.6, 0.5321),
+        "batch:V64/H32/pre/qb0/nd/u32": (551.9, 0.5356),
+        "batch:V64/H8/rec/qb0/nd/u32": (239.3, 0.5582),
     },
 }
 
@@ -352,6 +352,7 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
     members = [Tissue(r.tissue) for r in runs]
     torch.cuda.synchronize()
     bt = Batch(members)
+    bt.set_overlap(not args.sequential_classes)
     burn = int(round(args.batch_burn_in / dt))
     t_burn = time.perf_counter()
     if burn:
@@ -375,7 +376,7 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
     starts = {i: members[i].read_counts() for i in sample}
 
     ev0 = _events(members)
-    step_ms, class_ms, wm_ms = [], np.zeros(len(classes)), 0.0
+    step_ms, class_ms, chi_ms = [], np.zeros(len(classes)), 0.0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -389,8 +390,8 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
             b.record(bt.stream)
             b.synchronize()
             step_ms.append(a.elapsed_time(b))
-            _, w, cls = bt.read_timing()
-            wm_ms += w
+            _, c, _, cls = bt.read_timing()
+            chi_ms += c
             class_ms += np.array(cls)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t_wall
@@ -404,22 +405,47 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
     cells = sum(r.tissue.cells for r in runs)
     after = {i: (members[i].read_counts(), *members[i].read_stats()) for i in sample}
 
-    # per-class chi events and rooflines; the dominant class is the one with
-    # the largest chi time
-    per_class = []
+    # the chi phase's classes run overlapped (one launch per class, all
+    # ready at the phase's start): the roofline covers the phase as a whole,
+    # warp instructions of every class (its events x its measured
+    # instructions per event) over the phase's live time; a class's span
+    # runs from when its launch became ready (overlapped: the phase's start)
+    # to its last block
+    per_class, inst, traffic, stale = [], 0.0, 0.0, False
     for ci, c in enumerate(classes):
         idx = [i for i, r in enumerate(runs) if r.tissue.V == c["V"]]
         key = chi_kernel_key(c["V"], c["lanes_per_cell"], c["smem_layout"])
-        rl = issue_roofline("batch", float(d_ev[idx, 0].sum()), float(class_ms[ci]), key, c["V"],
-                            c["cells"], args.steps, args.steps)
+        ev_c = float(d_ev[idx, 0].sum())
+        m = chi_ipe("batch", key)
+        if m is None:
+            stale = True
+        else:
+            inst += ev_c * m[0]
+            traffic = None if traffic is None or m[1] is None else traffic + ev_c * m[1]
         per_class.append({"V": c["V"], "cells": c["cells"], "tissues": len(idx),
                           "launch": [c["lanes_per_cell"], c["warps_per_block"], c["smem_layout"]],
-                          "chi_ms_per_step": class_ms[ci] / args.steps,
-                          "chi_events_per_step": float(d_ev[idx, 0].sum()) / args.steps,
-                          "roofline": rl})
-    dom = max(range(len(per_class)), key=lambda i: per_class[i]["chi_ms_per_step"])
-    roofline = dict(per_class[dom]["roofline"])
-    roofline["class_V"] = per_class[dom]["V"]
+                          "kernel": f"k_chi_seg {key}",
+                          "span_ms_per_step": class_ms[ci] / args.steps,
+                          "chi_events_per_step": ev_c / args.steps,
+                          "inst_per_event": None if m is None else m[0]})
+    peaks, peak_kind = _peaks()
+    chi_s = chi_ms / 1e3
+    chi_events = float(d_ev[:, 0].sum())
+    hbm = sum(24 * c["V"] * c["cells"] for c in classes) * args.steps / chi_s / 1e9
+    roofline = {"bound": "alu", "unit": "Gwarp-inst/s", "peak": ISSUE_PEAK_GINST,
+                "peak_source": "152 SMs x 4 issue/clk x 2.070 GHz",
+                "kernel": "k_chi_seg, one launch per cell-size class, " +
+                          ("one after another" if args.sequential_classes else "overlapped"),
+                "chi_events_per_s": chi_events / chi_s, "launch_ms": chi_ms / args.steps,
+                "hbm_gbs": hbm, "hbm_frac": hbm / peaks["hbm_gbs"], "hbm_peak_source": peak_kind}
+    if stale:
+        roofline.update({"achieved": None, "frac": None, "traffic": None, "inst_per_event": None,
+                         "stale": "no instruction count measured on the current kernel sources"})
+    else:
+        ach = inst / chi_s / 1e9
+        roofline.update({"achieved": ach, "frac": ach / ISSUE_PEAK_GINST,
+                         "inst_per_event": inst / chi_events,
+                         "traffic": None if traffic is None else traffic / args.steps})
 
     # end to end through the C ABI: every tissue's state from pinned host
     # memory before each step, back to pinned host memory after it (the
@@ -523,6 +549,7 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
                    "state_bytes": sum(r.tissue.state_ints * 4 for r in runs),
                    "l2": "state (~2 GB) larger than L2; no flush",
                    "parallelism": f"replicas x{world}", "graph": "one step per captured graph",
+                   "classes_overlapped": not args.sequential_classes,
                    "tuned": None if not tuned else {
                        "classes": {str(k): list(v) for k, v in tuned["classes"].items()},
                        "steps_per_graph": tuned["steps_per_graph"]}},
@@ -530,7 +557,8 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
         "events_per_step": events_job / args.steps,
         "chi_events_per_step": float(d_ev[:, 0].sum()) / args.steps,
         "step_ms_median": statistics.median(step_ms), "step_ms_max": max(step_ms),
-        "sig_ms_per_step": (total_ms - class_ms.sum() - wm_ms) / args.steps,
+        "chi_ms_per_step": chi_ms / args.steps,
+        "sig_ms_per_step": (total_ms - chi_ms) / args.steps,
         "classes": per_class,
         "e2e": e2e,
         "gpu_launches": None,
@@ -935,6 +963,9 @@ def run_profile(args) -> dict:
     torch.cuda.synchronize()
     if args.profile_chi == "batch":
         bt = Batch(members)
+        # classes one after another, so that the profiler's launch order is
+        # the class order (instructions per event do not depend on overlap)
+        bt.set_overlap(False)
         for part in args.profile_class:  # V:lanes:warps:layout, e.g. an autotuner pick
             V, lanes, wpb, layout = (int(x) for x in part.split(":"))
             bt.set_class_launch(V, lanes, wpb, layout)
@@ -1104,6 +1135,9 @@ def main():
     ap.add_argument("--batch-burn-in", type=float, default=5.0,
                     help="untimed simulated time of the batch before its timed steps")
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--sequential-classes", action="store_true",
+                    help="run the batch's cell-size classes one after another instead of "
+                         "overlapped (their live times then separate)")
     ap.add_argument("--tune-clones", type=int, default=8,
                     help="member tissues per cell-size class the autotuner clones")
     ap.add_argument("--e2e-steps", type=int, default=3)

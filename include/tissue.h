@@ -312,13 +312,26 @@ int tissue_batch_class_info(const tissue_batch* b, uint32_t i, uint32_t* V,
  * never depend on it.  Toggling it drops the captured graph. */
 int tissue_batch_set_timing(tissue_batch* b, uint32_t on);
 
-/* Device milliseconds of the last step enqueued with timing on: the whole
- * step, the well-mixed chi launch (0 when the batch has no well-mixed cell)
- * and the chi launches of each class i < n (the 16-bit-count launch and its
- * 32-bit redo pass together).  Waits for the batch stream.  TISSUE_E_ARG if
- * timing is off or no timed step has run. */
-int tissue_batch_read_timing(tissue_batch* b, double* step_ms, double* wm_ms, double* class_ms,
-                             uint32_t n);
+/* Device milliseconds of the last step enqueued with timing on (any pointer
+ * may be NULL): the whole step; the chi phase (well-mixed and lattice
+ * classes); the well-mixed chi launch (0 when the batch has no well-mixed
+ * cell); and for each class i < n its chi launches (the 16-bit-count launch
+ * and its 32-bit redo pass together), from when they became ready to run to
+ * their end.  Classes run one after another, or overlapped (see
+ * tissue_batch_set_overlap): then every class is ready from the start of the
+ * chi phase, and a class that waits for SMs held by another counts that wait.
+ * Waits for the batch stream.  TISSUE_E_ARG if timing is off or no timed
+ * step has run. */
+int tissue_batch_read_timing(tissue_batch* b, double* step_ms, double* chi_ms, double* wm_ms,
+                             double* class_ms, uint32_t n);
+
+/* Overlapped classes (on = 1, the default) or one after another (0).  The
+ * chi launches of a step's classes run on separate streams: the first class
+ * (the largest cells, which take longest) at the device's highest launch
+ * priority, the others at the lowest, so their blocks fill the SMs the first
+ * class's last wave frees instead of waiting for its slowest cells.  Results
+ * never depend on it.  Changing it drops the captured graph. */
+int tissue_batch_set_overlap(tissue_batch* b, uint32_t on);
 
 void tissue_batch_destroy(tissue_batch* b);
 

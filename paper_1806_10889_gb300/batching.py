@@ -98,13 +98,19 @@ class Batch:
         _check(lib().tissue_batch_set_timing(self._h, 1 if on else 0), "tissue_batch_set_timing")
 
     def read_timing(self):
-        """(step ms, well-mixed chi ms, [chi ms per class]) of the last timed step."""
+        """(step ms, chi phase ms, well-mixed chi ms, [chi ms per class]) of
+        the last timed step (a class's time runs from when its launches became
+        ready; overlapped classes are all ready at the chi phase's start)."""
         n = self.info()[1]
-        st, wm = C.c_double(), C.c_double()
+        st, chi, wm = C.c_double(), C.c_double(), C.c_double()
         cls = (C.c_double * max(n, 1))()
-        _check(lib().tissue_batch_read_timing(self._h, C.byref(st), C.byref(wm), cls, n),
-               "tissue_batch_read_timing")
-        return st.value, wm.value, [cls[i] for i in range(n)]
+        _check(lib().tissue_batch_read_timing(self._h, C.byref(st), C.byref(chi), C.byref(wm),
+                                              cls, n), "tissue_batch_read_timing")
+        return st.value, chi.value, wm.value, [cls[i] for i in range(n)]
+
+    def set_overlap(self, on: bool) -> None:
+        """Overlapped cell-size classes (the default) or one after another."""
+        _check(lib().tissue_batch_set_overlap(self._h, 1 if on else 0), "tissue_batch_set_overlap")
 
     def total_events(self) -> int:
         return int(sum(int(m.total_events().sum()) for m in self.members))

@@ -51,7 +51,7 @@ cudaError_t launch_one(ChiSegKernel k, const TissueView* d_views, const uint2* d
                        uint32_t n_items, const uint32_t* n_dev, uint32_t* d_counter,
                        uint32_t seg_bytes, int H, int warps_per_block, int blocks,
                        uint32_t step_off, double dt, uint2* redo, uint32_t* redo_n,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, int priority) {
   const size_t smem = static_cast<size_t>(warps_per_block) * (32 / H) * seg_bytes;
   const int threads = 32 * warps_per_block;
   cudaError_t e = cudaSuccess;
@@ -70,9 +70,24 @@ cudaError_t launch_one(ChiSegKernel k, const TissueView* d_views, const uint2* d
     const uint32_t need = (n_items + segs_per_block - 1) / segs_per_block;
     if (need < static_cast<uint32_t>(blocks)) blocks = static_cast<int>(need);
   }
-  k<<<blocks, threads, smem, stream>>>(d_views, d_items, n_items, d_counter, seg_bytes, step_off,
-                                       dt, redo, redo_n, n_dev);
-  return cudaGetLastError();
+  if (priority == 0) {
+    k<<<blocks, threads, smem, stream>>>(d_views, d_items, n_items, d_counter, seg_bytes,
+                                         step_off, dt, redo, redo_n, n_dev);
+    return cudaGetLastError();
+  }
+  // a launch priority (kept by a captured kernel node as its attribute)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+  cfg.blockDim = dim3(static_cast<unsigned>(threads));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = priority;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, d_views, d_items, n_items, d_counter, seg_bytes, step_off, dt,
+                            redo, redo_n, n_dev);
 }
 
 }  // namespace
@@ -80,7 +95,7 @@ cudaError_t launch_one(ChiSegKernel k, const TissueView* d_views, const uint2* d
 cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
                            uint32_t* d_counter, uint32_t vmax_cells, int H, int warps_per_block,
                            int blocks, uint32_t step_off, double dt, bool pre, int gen,
-                           const ChiRedo* redo, cudaStream_t stream) {
+                           const ChiRedo* redo, cudaStream_t stream, int priority) {
   if (n_items == 0) return cudaSuccess;
   if (H != 8 && H != 16 && H != 32) return cudaErrorInvalidValue;
   if (!pre && warps_per_block > 4) return cudaErrorInvalidValue;
@@ -101,13 +116,14 @@ cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint
       (redo && gen == 0 && vmax_cells > 256) ? chi_seg_kernel_narrow(H, pre, qb) : nullptr;
   if (!kn)
     return launch_one(k, d_views, d_items, n_items, nullptr, d_counter, seg_bytes, H,
-                      warps_per_block, blocks, step_off, dt, nullptr, nullptr, stream);
+                      warps_per_block, blocks, step_off, dt, nullptr, nullptr, stream, priority);
   cudaError_t e = launch_one(kn, d_views, d_items, n_items, nullptr, d_counter,
                              seg_bytes_for(vmax_cells, H, pre, true), H, warps_per_block, blocks,
-                             step_off, dt, redo->items, redo->counters + 1, stream);
+                             step_off, dt, redo->items, redo->counters + 1, stream, priority);
   if (e != cudaSuccess) return e;
   return launch_one(k, d_views, redo->items, n_items, redo->counters + 1, redo->counters + 2,
-                    seg_bytes, H, warps_per_block, blocks, step_off, dt, nullptr, nullptr, stream);
+                    seg_bytes, H, warps_per_block, blocks, step_off, dt, nullptr, nullptr, stream,
+                    priority);
 }
 
 }  // namespace tsg

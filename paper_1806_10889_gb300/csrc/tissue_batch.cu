@@ -59,19 +59,37 @@ struct tissue_batch {
   uint32_t scheme = TISSUE_SPLIT_LIE;
   // timing (tissue_batch_set_timing): events at the step's start and end,
   // before the well-mixed launch and after it, and after each class
-  bool timing = false, timed_once = false;
-  std::vector<cudaEvent_t> tev;  // [0] step start, [1] step end, [2] chi start, [3 + i] after part i
+  bool timing = false, timed_once = false, timed_overlap = false;
+  // [0] step start, [1] step end, [2] chi start, [3] after the well-mixed
+  // launch (the classes' start), [4 + i] end of class i, [4 + classes] chi end
+  std::vector<cudaEvent_t> tev;
+  // Overlapped classes: the largest-cell class runs on the batch stream at
+  // the highest launch priority; every other class on a stream of its own at
+  // the lowest, forked after the well-mixed launch and joined before the
+  // faces, so its blocks take the SMs the large class's last wave frees.
+  bool overlap = true;
+  std::vector<cudaStream_t> side;  // one per class after the first
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
+  int prio_hi = 0, prio_lo = 0;
 };
 
 namespace {
 
 // Record timing event i on the batch stream (an event-record node when the
 // stream is being captured).
-int mark(tissue_batch* b, size_t i) {
+int mark(tissue_batch* b, size_t i, cudaStream_t stream) {
   if (!b->timing) return TISSUE_OK;
-  return cudaEventRecordWithFlags(b->tev[i], b->stream, cudaEventRecordExternal) == cudaSuccess
+  return cudaEventRecordWithFlags(b->tev[i], stream, cudaEventRecordExternal) == cudaSuccess
              ? TISSUE_OK
              : TISSUE_E_CUDA;
+}
+
+int mark(tissue_batch* b, size_t i) { return mark(b, i, b->stream); }
+
+bool overlapped(const tissue_batch* b) {
+  return b->overlap && b->stream != nullptr && b->classes.size() > 1 &&
+         b->side.size() + 1 == b->classes.size();
 }
 
 int chi_all(tissue_batch* b, double dt) {
@@ -80,12 +98,18 @@ int chi_all(tissue_batch* b, double dt) {
                                b->stream) != cudaSuccess)
     return TISSUE_E_CUDA;
   if (mark(b, 3) != TISSUE_OK) return TISSUE_E_CUDA;
-  for (size_t c = 0; c < b->classes.size(); ++c) {
+  const size_t nc = b->classes.size();
+  const bool ov = overlapped(b);
+  if (ov && cudaEventRecord(b->ev_fork, b->stream) != cudaSuccess) return TISSUE_E_CUDA;
+  for (size_t c = 0; c < nc; ++c) {
     const ClassPlan& p = b->classes[c];
+    const cudaStream_t st = (ov && c > 0) ? b->side[c - 1] : b->stream;
+    if (ov && c > 0 && cudaStreamWaitEvent(st, b->ev_fork, 0) != cudaSuccess) return TISSUE_E_CUDA;
     uint32_t* counters = b->d_counters + 3 * c;
-    if (cudaMemsetAsync(counters, 0, 3 * sizeof(uint32_t), b->stream) != cudaSuccess)
+    if (cudaMemsetAsync(counters, 0, 3 * sizeof(uint32_t), st) != cudaSuccess)
       return TISSUE_E_CUDA;
-    const ChiRedo redo{b->d_redo, counters};
+    // each class has its own part of the redo list (classes may run at once)
+    const ChiRedo redo{b->d_redo + p.items_off, counters};
     // as for single tissues: a counts-only launch with several voxels per
     // lane takes Notch-Delta classes without a trace; others run the prefix
     // launch of the class (the same trajectories)
@@ -93,13 +117,22 @@ int chi_all(tissue_batch* b, double dt) {
     if (lc.smem_layout == TISSUE_LAYOUT_RECOMPUTE &&
         !recompute_covers(p.V, static_cast<int>(p.lanes), p.gen))
       lc = prefix_launch(p.V, p.n_items);
+    const int prio = ov ? (c == 0 ? b->prio_hi : b->prio_lo) : 0;
     if (launch_chi_seg(b->d_views, b->d_items + p.items_off, p.n_items, counters, p.V,
                        static_cast<int>(lc.lanes_per_cell), static_cast<int>(lc.warps_per_block),
-                       0, 0u, dt, lc.smem_layout == TISSUE_LAYOUT_PREFIX, p.gen, &redo,
-                       b->stream) != cudaSuccess)
+                       0, 0u, dt, lc.smem_layout == TISSUE_LAYOUT_PREFIX, p.gen, &redo, st,
+                       prio) != cudaSuccess)
       return TISSUE_E_CUDA;
-    if (mark(b, 4 + c) != TISSUE_OK) return TISSUE_E_CUDA;
+    if (mark(b, 4 + c, st) != TISSUE_OK) return TISSUE_E_CUDA;
+    if (ov && c > 0 && cudaEventRecord(b->ev_join[c - 1], st) != cudaSuccess)
+      return TISSUE_E_CUDA;
   }
+  if (ov)
+    for (size_t c = 1; c < nc; ++c)
+      if (cudaStreamWaitEvent(b->stream, b->ev_join[c - 1], 0) != cudaSuccess)
+        return TISSUE_E_CUDA;
+  if (mark(b, 4 + nc) != TISSUE_OK) return TISSUE_E_CUDA;
+  if (b->timing) b->timed_overlap = ov;
   return TISSUE_OK;
 }
 
@@ -134,6 +167,35 @@ int enqueue_step(tissue_batch* b, double dt) {
 void drop_events(tissue_batch* b) {
   for (cudaEvent_t e : b->tev) cudaEventDestroy(e);
   b->tev.clear();
+}
+
+// The side streams and fork/join events of overlapped classes.
+void drop_side(tissue_batch* b) {
+  for (cudaStream_t st : b->side) cudaStreamDestroy(st);
+  b->side.clear();
+  for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
+  b->ev_join.clear();
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  b->ev_fork = nullptr;
+}
+
+bool make_side(tissue_batch* b) {
+  if (b->classes.size() < 2) return true;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return false;
+  b->prio_lo = least;
+  b->prio_hi = greatest;
+  if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) return false;
+  for (size_t c = 1; c < b->classes.size(); ++c) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, least) != cudaSuccess)
+      return false;
+    b->side.push_back(st);
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
+    b->ev_join.push_back(ev);
+  }
+  return true;
 }
 
 void drop_graph(tissue_batch* b) {
@@ -215,8 +277,8 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
 
   const size_t views_bytes = (sizeof(TissueView) * count + 255) & ~static_cast<size_t>(255);
   const size_t items_bytes = (sizeof(uint2) * items.size() + 255) & ~static_cast<size_t>(255);
-  size_t redo_items = 0;  // the classes run one after another and share the redo list
-  for (const ClassPlan& p : b->classes) redo_items = std::max<size_t>(redo_items, p.n_items);
+  size_t redo_items = 0;  // every class has its part (at its items' offset)
+  for (const ClassPlan& p : b->classes) redo_items = std::max<size_t>(redo_items, p.items_off + p.n_items);
   const size_t redo_bytes = (sizeof(uint2) * redo_items + 255) & ~static_cast<size_t>(255);
   const size_t io_bytes = (2 * sizeof(uint32_t) * count + 255) & ~static_cast<size_t>(255);
   const size_t counters_bytes =
@@ -250,12 +312,14 @@ int tissue_batch_create(tissue* const* members, uint32_t count, void* cuda_strea
   // Members' pending work (creation, earlier steps) must finish before the
   // batch stream uses their buffers.
   auto fail = [b]() {
+    drop_side(b);
     cudaFreeHost(b->h_io_steps);
     cudaFreeHost(b->h_io_flags);
     cudaFree(b->dmem);
     delete b;
     return TISSUE_E_CUDA;
   };
+  if (!make_side(b)) return fail();
   for (uint32_t i = 0; i < count; ++i)
     if (cudaStreamSynchronize(info[i].stream) != cudaSuccess) return fail();
   if (cudaMemcpy(b->d_views, views.data(), sizeof(TissueView) * count, cudaMemcpyHostToDevice) !=
@@ -318,7 +382,9 @@ int tissue_batch_step(tissue_batch* b, double dt, uint32_t n_steps) {
       if (g) cudaGraphDestroy(g);
       return TISSUE_E_CUDA;
     }
-    const cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+    // node priorities: the overlapped large-cell class goes first
+    const cudaError_t ie =
+        cudaGraphInstantiateWithFlags(&b->graph, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (ie != cudaSuccess) {
       b->graph = nullptr;
@@ -446,7 +512,7 @@ int tissue_batch_set_timing(tissue_batch* b, uint32_t on) {
   b->timing = false;
   b->timed_once = false;
   if (!on) return TISSUE_OK;
-  const size_t n = 4 + b->classes.size();
+  const size_t n = 5 + b->classes.size();
   for (size_t i = 0; i < n; ++i) {
     cudaEvent_t e = nullptr;
     if (cudaEventCreate(&e) != cudaSuccess) {
@@ -459,25 +525,33 @@ int tissue_batch_set_timing(tissue_batch* b, uint32_t on) {
   return TISSUE_OK;
 }
 
-int tissue_batch_read_timing(tissue_batch* b, double* step_ms, double* wm_ms, double* class_ms,
-                             uint32_t n) {
+int tissue_batch_read_timing(tissue_batch* b, double* step_ms, double* chi_ms, double* wm_ms,
+                             double* class_ms, uint32_t n) {
   if (!b || !b->timing || !b->timed_once || n > b->classes.size()) return TISSUE_E_ARG;
   if (n > 0 && !class_ms) return TISSUE_E_ARG;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TISSUE_E_CUDA;
   float ms = 0.0f;
-  if (step_ms) {
-    if (cudaEventElapsedTime(&ms, b->tev[0], b->tev[1]) != cudaSuccess) return TISSUE_E_CUDA;
-    *step_ms = ms;
-  }
-  if (wm_ms) {
-    if (cudaEventElapsedTime(&ms, b->tev[2], b->tev[3]) != cudaSuccess) return TISSUE_E_CUDA;
-    *wm_ms = ms;
-  }
+  auto span = [&](size_t a, size_t z, double* out) -> bool {
+    if (!out) return true;
+    if (cudaEventElapsedTime(&ms, b->tev[a], b->tev[z]) != cudaSuccess) return false;
+    *out = ms;
+    return true;
+  };
+  const size_t nc = b->classes.size();
+  if (!span(0, 1, step_ms) || !span(2, 4 + nc, chi_ms) || !span(2, 3, wm_ms)) return TISSUE_E_CUDA;
   for (uint32_t i = 0; i < n; ++i) {
-    if (cudaEventElapsedTime(&ms, b->tev[3 + i], b->tev[4 + i]) != cudaSuccess)
-      return TISSUE_E_CUDA;
-    class_ms[i] = ms;
+    // a class starts when its launches become ready: after the previous
+    // class, or, overlapped, when the classes fork
+    const size_t from = (b->timed_overlap || i == 0) ? 3 : 3 + i;
+    if (!span(from, 4 + i, class_ms + i)) return TISSUE_E_CUDA;
   }
+  return TISSUE_OK;
+}
+
+int tissue_batch_set_overlap(tissue_batch* b, uint32_t on) {
+  if (!b || on > 1) return TISSUE_E_ARG;
+  if ((on != 0) != b->overlap) drop_graph(b);
+  b->overlap = on != 0;
   return TISSUE_OK;
 }
 
@@ -499,6 +573,7 @@ void tissue_batch_destroy(tissue_batch* b) {
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
   drop_events(b);
+  drop_side(b);
   cudaFreeHost(b->h_io_steps);
   cudaFreeHost(b->h_io_flags);
   cudaFree(b->dmem);

@@ -121,7 +121,7 @@ struct ChiRedo {
 cudaError_t launch_chi_seg(const TissueView* d_views, const uint2* d_items, uint32_t n_items,
                            uint32_t* d_counter, uint32_t vmax_cells, int H, int warps_per_block,
                            int blocks, uint32_t step_off, double dt, bool pre, int gen,
-                           const ChiRedo* redo, cudaStream_t stream);
+                           const ChiRedo* redo, cudaStream_t stream, int priority = 0);
 using ChiSegKernel = void (*)(const TissueView*, const uint2*, uint32_t, uint32_t*, uint32_t,
                               uint32_t, double, uint2*, uint32_t*, const uint32_t*);
 ChiSegKernel chi_seg_kernel_nd(int H, bool pre, bool qb);   // k_chi_seg.cu

@@ -114,7 +114,8 @@ SIGNATURES = {
                                           _P(C.c_uint32)]),
     "tissue_batch_set_timing": (C.c_int, [C.c_void_p, C.c_uint32]),
     "tissue_batch_read_timing": (C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_double),
-                                           _P(C.c_double), C.c_uint32]),
+                                           _P(C.c_double), _P(C.c_double), C.c_uint32]),
+    "tissue_batch_set_overlap": (C.c_int, [C.c_void_p, C.c_uint32]),
     "tissue_batch_destroy": (None, [C.c_void_p]),
     "tissue_destroy": (None, [C.c_void_p]),
     "tissue_strerror": (C.c_char_p, [C.c_int]),

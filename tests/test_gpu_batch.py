@@ -31,11 +31,14 @@ MIX = [TissueSpec(3, 2, 8, seed=3, tissue_id=0).with_model(kD=7.5),
        TissueSpec(2, 3, 16, seed=3, tissue_id=5).with_model(kD=19.0)]
 
 
-@pytest.mark.parametrize("steps_per_graph", [1, 2])
-def test_batch_matches_oracle_per_member(steps_per_graph):
+@pytest.mark.parametrize("steps_per_graph,overlap", [(1, True), (2, True), (1, False)])
+def test_batch_matches_oracle_per_member(steps_per_graph, overlap):
+    """Both with the cell-size classes overlapped (the default) and with
+    them one after another."""
     members = [T.Tissue(s) for s in MIX]
     b = Batch(members)
     b.set_schedule(steps_per_graph)
+    b.set_overlap(overlap)
     assert b.info() == (len(MIX), 4, sum(s.cells for s in MIX))
     ref = [O.init_counts(orc_desc(s)) for s in MIX]
     dt = 0.1
@@ -126,13 +129,17 @@ def test_batch_timing_and_class_info_change_no_result():
             b.set_timing(True)
             with pytest.raises(T.TissueError):
                 b.read_timing()  # no timed step yet
-        for _ in range(3):
+        for k in range(4):
+            if timing:
+                b.set_overlap(k < 2)  # overlapped classes, then one after another
             b.step(0.1, 1)
             if timing:
-                step_ms, wm_ms, class_ms = b.read_timing()
+                step_ms, chi_ms, wm_ms, class_ms = b.read_timing()
                 assert step_ms > 0 and wm_ms >= 0 and len(class_ms) == len(cls)
                 assert all(x > 0 for x in class_ms)
-                assert sum(class_ms) + wm_ms <= step_ms * 1.001
+                assert chi_ms <= step_ms * 1.001 and max(class_ms) <= chi_ms * 1.001
+                if k >= 2:  # one after another: the classes add up to the chi phase
+                    assert abs(sum(class_ms) + wm_ms - chi_ms) <= 0.01 * chi_ms + 0.05
         b.sync()
         outs.append([m.read_counts() for m in members])
         if timing:

@@ -352,7 +352,6 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
     members = [Tissue(r.tissue) for r in runs]
     torch.cuda.synchronize()
     bt = Batch(members)
-    bt.set_overlap(not args.sequential_classes)
     burn = int(round(args.batch_burn_in / dt))
     t_burn = time.perf_counter()
     if burn:
@@ -365,6 +364,13 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
         autotune.apply_batch(bt, tuned)
     # the timed steps replay one step per graph so that each is timed
     bt.set_schedule(1)
+    # overlapped or sequential classes: chosen from 4 steps of the batch
+    # itself (before the warm-up steps), or forced
+    overlap_tune = None
+    if args.class_overlap == "auto":
+        overlap_tune = autotune.tune_overlap(bt, dt)
+    else:
+        bt.set_overlap(args.class_overlap == "on")
     bt.set_timing(True)
     for _ in range(args.warmup):
         bt.step(dt, 1)
@@ -435,7 +441,7 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
     roofline = {"bound": "alu", "unit": "Gwarp-inst/s", "peak": ISSUE_PEAK_GINST,
                 "peak_source": "152 SMs x 4 issue/clk x 2.070 GHz",
                 "kernel": "k_chi_seg, one launch per cell-size class, " +
-                          ("one after another" if args.sequential_classes else "overlapped"),
+                          ("overlapped" if bt.overlap else "one after another"),
                 "chi_events_per_s": chi_events / chi_s, "launch_ms": chi_ms / args.steps,
                 "hbm_gbs": hbm, "hbm_frac": hbm / peaks["hbm_gbs"], "hbm_peak_source": peak_kind}
     if stale:
@@ -549,7 +555,7 @@ def batch_headline(args, rank: int, world: int, dist) -> dict:
                    "state_bytes": sum(r.tissue.state_ints * 4 for r in runs),
                    "l2": "state (~2 GB) larger than L2; no flush",
                    "parallelism": f"replicas x{world}", "graph": "one step per captured graph",
-                   "classes_overlapped": not args.sequential_classes,
+                   "classes_overlapped": bt.overlap, "overlap_tuning": overlap_tune,
                    "tuned": None if not tuned else {
                        "classes": {str(k): list(v) for k, v in tuned["classes"].items()},
                        "steps_per_graph": tuned["steps_per_graph"]}},
@@ -1135,9 +1141,10 @@ def main():
     ap.add_argument("--batch-burn-in", type=float, default=5.0,
                     help="untimed simulated time of the batch before its timed steps")
     ap.add_argument("--autotune", type=int, default=1)
-    ap.add_argument("--sequential-classes", action="store_true",
-                    help="run the batch's cell-size classes one after another instead of "
-                         "overlapped (their live times then separate)")
+    ap.add_argument("--class-overlap", choices=["auto", "on", "off"], default="auto",
+                    help="the batch's cell-size classes overlapped or one after another "
+                         "(off: their live times separate); auto picks the faster from "
+                         "4 steps of the batch before the warm-up")
     ap.add_argument("--tune-clones", type=int, default=8,
                     help="member tissues per cell-size class the autotuner clones")
     ap.add_argument("--e2e-steps", type=int, default=3)

@@ -22,6 +22,8 @@ class Batch:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         arr = (C.c_void_p * len(members))(*[m.handle.value for m in members])
         self._h = C.c_void_p()
+        self.timing = False  # tissue_batch_set_timing's state
+        self.overlap = True  # tissue_batch_set_overlap's state
         _check(lib().tissue_batch_create(arr, len(members), C.c_void_p(self.stream.cuda_stream),
                                          C.byref(self._h)), "tissue_batch_create")
 
@@ -96,6 +98,7 @@ class Batch:
     def set_timing(self, on: bool) -> None:
         """Record device times of each following step (a measurement aid)."""
         _check(lib().tissue_batch_set_timing(self._h, 1 if on else 0), "tissue_batch_set_timing")
+        self.timing = bool(on)
 
     def read_timing(self):
         """(step ms, chi phase ms, well-mixed chi ms, [chi ms per class]) of
@@ -111,6 +114,7 @@ class Batch:
     def set_overlap(self, on: bool) -> None:
         """Overlapped cell-size classes (the default) or one after another."""
         _check(lib().tissue_batch_set_overlap(self._h, 1 if on else 0), "tissue_batch_set_overlap")
+        self.overlap = bool(on)
 
     def total_events(self) -> int:
         return int(sum(int(m.total_events().sum()) for m in self.members))

@@ -189,3 +189,29 @@ def test_batch_state_io_matches_per_member_io():
     b.close()
     for m in members:
         m.close()
+
+
+def test_overlap_tuning_picks_a_mode_and_keeps_the_trajectory():
+    """autotune.tune_overlap steps the batch 4 times, alternating overlapped
+    and sequential classes, and leaves the faster set; the members still
+    match the oracle bit for bit."""
+    from paper_1806_10889_gb300 import autotune
+    members = [T.Tissue(s) for s in MIX]
+    b = Batch(members)
+    dt = 0.1
+    res = autotune.tune_overlap(b, dt)
+    assert set(res["ms"]) == {"overlapped", "sequential"}
+    assert all(v > 0 for v in res["ms"].values())
+    assert b.overlap == res["overlap"] and b.timing is False
+    assert all(m.get_step() == 4 for m in members)
+    b.step(dt, 1)
+    b.sync()
+    for i, s in enumerate(MIX):
+        ref = O.init_counts(orc_desc(s))
+        ne, tl = O.step(orc_desc(s), orc_model(s), ref, 0, 5, dt)
+        assert np.array_equal(members[i].read_counts(), ref), i
+        gne, gtl = members[i].read_stats()
+        assert np.array_equal(gne, ne) and np.array_equal(_bits(gtl), _bits(tl)), i
+    b.close()
+    for m in members:
+        m.close()

@@ -54,6 +54,7 @@ struct Seg {
   uint32_t magic;
   int qb;           // log2 of the voxels each lane covers inside one block (B > H)
   int centre;       // the promoter voxel (n/2, n/2)
+  int ls;           // log2 of a sub-block's voxels, lb - qb (counts-only layout, B > H)
 };
 
 // The model terms c0, c1 and X of a voxel (see the file comment); hR is the
@@ -241,12 +242,17 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (QB ? 4 : (NARROW ?
   LaneK lk{}, lk2{};                         // their coefficients for the current cell
   HillRegs<H, (!PRE && H == 8) ? 2 : (H == 32 || (!PRE && H == 16)) ? 1 : 0> hreg;
 
-  // The counts-only layout covers up to four voxels of a block per lane
-  // (B > H) with 16 lanes (V <= 1024) or 8 lanes (V <= 256).
+  // The counts-only layout with blocks wider than the segment (B > H, up to
+  // four sub-blocks of H voxels: 16 lanes for V <= 1024, 8 for V <= 256):
+  // lane l keeps the running sums sb[k] of its own block's sub-blocks 0..k,
+  // so that an event finds the sub-block from lane L's sums and recomputes
+  // only its H voxels, one per lane, instead of the whole block.
   static_assert(PRE || !QB || H == 16 || H == 8, "recompute layout with B > H: 8 or 16 lanes");
+  constexpr bool SUB = !PRE && QB;
+  uint64_t sb[4] = {0ull, 0ull, 0ull, 0ull};
   bool have = false, done = false, pm = false;
   bool oob = false;  // checked build: an index out of range (see TSG_IDX)
-  Seg s{0, 2, 1, 0, 1, 0, 0};
+  Seg s{0, 2, 1, 0, 1, 0, 0, 0};
   uint32_t cell = 0, vidx = 0, step = 0, word3 = 0, key0 = 0, key1 = 0, e = 0, e0 = 0;
   uint64_t A = 0, P = 0, Em = 0, Rb = 0, Em2 = 0, Rb2 = 0;
   int Ek = -1, Ek2 = -1, err = 0;
@@ -279,6 +285,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (QB ? 4 : (NARROW ?
         s.qb = 0;
         while ((H << s.qb) < s.B) ++s.qb;
         s.centre = (s.n >> 1) * s.n + (s.n >> 1);
+        s.ls = s.lb - s.qb;
         pm = GEN == 2 || (GEN == 1 && sv->q.kind == kModelPromoter);
         lk = lane_k(cl, sv->q);
         if (H == 8) lk2 = lane_k(cl2, sv->q);
@@ -334,6 +341,14 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (QB ? 4 : (NARROW ?
               if (pm && cnt[2 * vmax + v] > static_cast<int32_t>(v == s.centre)) bad_state = true;
               S += seg_voxel_total<(GEN != 0)>(cnt, vmax, v, s, sv->q, pm, ovf, oob);
               if (PRE) pre[TSG_IDX(v, vmax, oob)] = S;
+            }
+            if (SUB && ((i + 1) & ((1 << s.ls) - 1)) == 0) {
+              // the end of sub-block i >> ls (voxels past V add nothing); the
+              // entries past the block's last sub-block end as its total
+              const int kk = i >> s.ls;
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                if (k >= kk) sb[k] = S;
             }
           }
           P = S;
@@ -412,71 +427,66 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (QB ? 4 : (NARROW ?
     const unsigned m1 = (__ballot_sync(kFull, r < P && act) >> (seg * H)) & kSegBits;
     const int L = m1 ? __ffs(m1) - 1 : 0;
     const uint64_t Pl = __shfl_sync(kFull, P, L > 0 ? L - 1 : 0, H);
-    const uint64_t r1 = r - (L > 0 ? Pl : 0ull);
-    const int vb = L << s.lb;
+    uint64_t r1 = r - (L > 0 ? Pl : 0ull);
+    // The second level searches the nsec voxels from vb, lane sl covering
+    // voxels vb + sl*2^lq .. + 2^lq - 1 (lq = qb in the prefix layout, else 0)
+    int vb = L << s.lb;
+    int nsec = s.B;
+    const int lq = PRE ? qb : 0;
     const QRates& q = sv->q;
     uint64_t pv = ~0ull;
-    uint64_t run[4] = {0ull, 0ull, 0ull, 0ull};  // counts-only layout: a lane's running sums
+    bool bad_s = false;
     if (PRE) {
-      // lane sl covers voxels vb + sl*Q .. + Q-1 of the block (Q = 2^qb; 1 if B <= H)
       const int q0 = vb + (sl << qb);
       if ((sl << qb) < s.B && q0 < s.V)
         pv = pre[TSG_IDX(min(q0 + (1 << qb) - 1, s.V - 1), vmax, oob)];
     } else {
-      // the block's voxel propensities, recomputed: lane sl covers voxels
-      // vb + sl*Q .. + Q-1 (Q = 2^qb; Q = 1 unless QB), keeps their running
-      // sums in run[], and the lanes' totals are then scanned across the
-      // segment
-      constexpr int kQ = QB ? 4 : 1;
-      bool unused = false;
-      uint64_t acc = 0ull;
+      if (SUB) {
+        // the sub-block of lane L's block that holds r1: every lane finds
+        // the first of its own running sums above r1, and lane L's answer is
+        // taken (an empty sub-block is never chosen: its sum equals the one
+        // before it)
+        int kq = -1;
+        uint64_t below = 0ull;
 #pragma unroll
-      for (int k = 0; k < kQ; ++k) {
-        const int off = (sl << qb) + k;
-        const bool mine = act && k < (1 << qb) && off < s.B && vb + off < s.V;
-        const int bx = mine ? vb + off : 0;
-        const int bi = static_cast<int>(TSG_IDX(bx, vmax, oob));
-        const uint32_t bD = static_cast<uint32_t>(cnt[bi]);
-        const uint32_t bN = static_cast<uint32_t>(cnt[vmax + bi]);
-        const uint32_t bR = static_cast<uint32_t>(cnt[2 * vmax + bi]);
-        const uint64_t bh = GEN == 2 ? 0ull : hreg.get(q, bR, mine && !PM);
-        acc += mine ? voxel_total_of<(GEN != 0)>(bx, bD, bN, bR, bh, s, q, PM, unused) : 0ull;
-        run[k] = acc;
+        for (int k = 3; k >= 0; --k)
+          if (k < (1 << qb) && r1 < sb[k]) {
+            kq = k;
+            below = k > 0 ? sb[k > 0 ? k - 1 : 0] : 0ull;
+          }
+        const int ks = __shfl_sync(kFull, kq, L, H);
+        const uint64_t bs = __shfl_sync(kFull, below, L, H);
+        bad_s = ks < 0;
+        if (ks > 0) {
+          vb += ks << s.ls;
+          r1 -= bs;
+        }
+        nsec = 1 << s.ls;
       }
-      uint64_t cx = acc;
+      // the propensities of those voxels, recomputed (one per lane) and
+      // scanned across the segment
+      bool unused = false;
+      const bool mine = act && sl < nsec && vb + sl < s.V;
+      const int bx = mine ? vb + sl : 0;
+      const int bi = static_cast<int>(TSG_IDX(bx, vmax, oob));
+      const uint32_t bD = static_cast<uint32_t>(cnt[bi]);
+      const uint32_t bN = static_cast<uint32_t>(cnt[vmax + bi]);
+      const uint32_t bR = static_cast<uint32_t>(cnt[2 * vmax + bi]);
+      const uint64_t bh = GEN == 2 ? 0ull : hreg.get(q, bR, mine && !PM);
+      uint64_t cx = mine ? voxel_total_of<(GEN != 0)>(bx, bD, bN, bR, bh, s, q, PM, unused) : 0ull;
 #pragma unroll
       for (int o = 1; o < H; o <<= 1) {
         const uint64_t y = __shfl_up_sync(kFull, cx, o, H);
         if (sl >= o) cx += y;
       }
-      if ((sl << qb) < s.B && vb + (sl << qb) < s.V) pv = cx;
+      if (sl < nsec && vb + sl < s.V) pv = cx;
     }
     const unsigned m2 = (__ballot_sync(kFull, r1 < pv) >> (seg * H)) & kSegBits;
     const int i2 = m2 ? __ffs(m2) - 1 : 0;
     const uint64_t pp = __shfl_sync(kFull, pv, i2 > 0 ? i2 - 1 : 0, H);
     uint64_t r2 = r1 - (i2 > 0 ? pp : 0ull);
-    int v = vb + (i2 << qb);
+    int v = vb + (i2 << lq);
     bool bad_q = false;
-    if (!PRE && QB) {
-      // the voxel inside lane i2's run of Q = 2^qb voxels: every lane finds
-      // the first of its own running sums above r2, and lane i2's answer is
-      // taken (an empty run of zero-propensity voxels is never chosen)
-      int kq = -1;
-      uint64_t below = 0ull;
-#pragma unroll
-      for (int k = 3; k >= 0; --k)
-        if (k < (1 << qb) && r2 < run[k]) {
-          kq = k;
-          below = k > 0 ? run[k > 0 ? k - 1 : 0] : 0ull;
-        }
-      const int ks = __shfl_sync(kFull, kq, i2, H);
-      const uint64_t bs = __shfl_sync(kFull, below, i2, H);
-      bad_q = ks < 0;
-      if (ks >= 0) {
-        v += ks;
-        r2 -= bs;
-      }
-    }
     if (PRE && QB) {
       // the voxel inside lane i2's run of Q = 2^qb voxels: the segment's
       // lanes read H of the run's prefix entries at a time and one ballot
@@ -504,7 +514,7 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (QB ? 4 : (NARROW ?
       v = pick < 0 ? v : pick;
     }
     const bool bad1 = act && Aa != 0ull &&
-                      (m1 == 0u || m2 == 0u || (i2 << qb) >= s.B || v >= s.V || bad_q);
+                      (m1 == 0u || m2 == 0u || (i2 << lq) >= nsec || v >= s.V || bad_q || bad_s);
     if (bad1 || v >= s.V) v = 0;
 
     // channel: closed-form running sums
@@ -628,10 +638,20 @@ __global__ void __launch_bounds__(PRE ? 256 : 128, PRE ? 1 : (QB ? 4 : (NARROW ?
       const int bv = v >> s.lb;
       P += sl >= bv ? dv : 0ull;
       A += dv;
+      if (SUB) {  // the owning lane's sub-block sums from v's sub-block on
+        const int kv = (v & (s.B - 1)) >> s.ls;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sb[k] += (sl == bv && k >= kv) ? dv : 0ull;
+      }
       if (u >= 0) {
         const int bu = u >> s.lb;
         P += sl >= bu ? du : 0ull;
         A += du;
+        if (SUB) {
+          const int ku = (u & (s.B - 1)) >> s.ls;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) sb[k] += (sl == bu && k >= ku) ? du : 0ull;
+        }
       }
       if (PRE && (sl << qb) < s.B) {
         // prefix entries from the changed voxel to the end of its block

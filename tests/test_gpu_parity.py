@@ -372,9 +372,11 @@ def test_tiny_step_length():
                                      (8, 9)])
 @pytest.mark.parametrize("wpb", [1, 2, 4])
 def test_counts_only_layout_with_several_voxels_per_lane(lanes, n, wpb):
-    """The counts-only layout with more voxels per block than lanes: every
-    lane recomputes 2 or 4 voxels of the selected block (16 lanes: V = 1024,
-    576, 400, 289; 8 lanes: V = 256, 144, 81; all but the first of each with
-    partly empty blocks), every step bit-exact with the oracle."""
+    """The counts-only layout with more voxels per block than lanes: each
+    block splits into 2 or 4 sub-blocks whose running sums the owning lane
+    keeps, and an event recomputes one sub-block, one voxel per lane (16
+    lanes: V = 1024, 576, 400, 289; 8 lanes: V = 256, 144, 81; all but the
+    first of each with partly empty blocks and sub-blocks), every step
+    bit-exact with the oracle."""
     spec = TissueSpec(3, 3, n, seed=300 + n, tissue_id=wpb).with_model(**STRONG)
     _run_both(spec, 0.1, 3, config=(T.KERNEL_PERSISTENT, lanes, wpb, 0, T.LAYOUT_RECOMPUTE))

@@ -182,8 +182,10 @@ __device__ __forceinline__ ChanLane chan_lane(int j) {
 
 // PRE selects the shared-memory layout: true keeps the within-block prefix
 // pre[] of the voxel propensities (20 B per voxel); false keeps only the
-// counts (12 B per voxel) and recomputes the selected block's propensities,
-// trading ~70 instructions per pass for ~40% more cells resident per SM.
+// counts (12 B per voxel, 6 with 16-bit counts) and recomputes, per event,
+// the propensities of the selected block -- or, when a block is wider than
+// the segment, of one sub-block of H voxels found from the owning lane's
+// sub-block sums -- one voxel per lane, so that more cells fit on an SM.
 // A lane's channel-sum coefficients for one tissue, in registers (set when the
 // segment takes a cell): the per-count terms of the channels up to the lane's.
 // The hop terms depend on the voxel's neighbours and are added per voxel.

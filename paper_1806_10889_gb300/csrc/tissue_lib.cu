@@ -158,11 +158,13 @@ tissue_launch tsg::prefix_launch(uint32_t V, uint64_t cells) {
 tissue_launch tsg::default_launch(uint32_t V, uint64_t cells) {
   // Cells of more than 256 voxels in launches of many waves: two cells per
   // warp in the counts-only layout (16-bit counts, 6.4 KB per cell: 32 cells
-  // per SM against 14 with the prefix layout) recomputing the selected block,
-  // four voxels per lane.  Same-box A/B, 256x256 cells of 32x32 voxels: 876
-  // -> 710 ms per chi step.  Fewer cells than about two waves of it keep one
-  // cell per warp, whose event chain is shorter.  Launches the counts-only
-  // layout cannot take (the promoter model, a trace) run prefix_launch.
+  // per SM against 14 with the prefix layout), each event recomputing one
+  // sub-block of the selected block, one voxel per lane.  Same-box A/B,
+  // 256x256 cells of 32x32 voxels: 876 ms per chi step with the prefix
+  // layout, 542 ms with this one.  Fewer cells than about two waves of it
+  // keep one cell per warp, whose event chain is shorter.  Launches the
+  // counts-only layout cannot take (the promoter model, a trace) run
+  // prefix_launch.
   if (V > 256 && V <= 1024 && cells >= kManyCells)
     return tissue_launch{TISSUE_KERNEL_PERSISTENT, 16, 2, 0, TISSUE_LAYOUT_RECOMPUTE};
   return prefix_launch(V, cells);

@@ -223,13 +223,16 @@ typedef struct {
 /* The default after tissue_create: persistent kernel; for a tissue of at
  * most 1024 cells 32 lanes and 2 warps per block, prefix layout (one cell per
  * warp: the shortest event chain, which sets the time when the machine is
- * not full); otherwise by cell size, 8 lanes and 4 warps per block for
- * V <= 64, 16 lanes and 4 warps for V <= 256 (prefix layout), and above
- * that 16 lanes, 2 warps per block and the recompute layout from 8192 cells
- * (more cells resident per SM), else 32 lanes and 2 warps, prefix layout.
- * A recompute launch with more voxels per block than lanes that the
- * tissue's model cannot take (the promoter model, a trace) runs that last
- * prefix launch instead; results never depend on it. */
+ * not full); otherwise by cell size: V <= 64, 8 lanes and 4 warps per block,
+ * prefix layout; 64 < V <= 256, 8 lanes, 2 warps per block and the recompute
+ * layout above 6080 cells, else 16 lanes and 4 warps, prefix layout;
+ * 256 < V <= 1024, 16 lanes, 2 warps per block and the recompute layout
+ * above 2128 cells, else 32 lanes and 2 warps, prefix layout (the recompute
+ * layout holds more cells per SM; the thresholds are one wave of the prefix
+ * launch on a 152-SM GB300).  A recompute launch with more voxels per block
+ * than lanes that the tissue's model cannot take (the promoter model, a
+ * trace) runs the prefix launch of its cell size instead; results never
+ * depend on it. */
 int tissue_set_launch_config(tissue* t, const tissue_launch* config);
 int tissue_get_launch_config(const tissue* t, tissue_launch* config);
 

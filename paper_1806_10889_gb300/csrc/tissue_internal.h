@@ -162,9 +162,13 @@ struct TissueInfo {
 bool tissue_info(const tissue* t, TissueInfo* out);
 // The default chi launch for `cells` cells of V voxels (one launch).
 constexpr uint64_t kFewCells = 1024;
-// From this many cells of more than 256 voxels the default launch takes the
-// counts-only layout with 16 lanes (about two waves of its 4,864 cells).
-constexpr uint64_t kManyCells = 8192;
+// Above these cell counts the default launch takes the counts-only layout:
+// past one wave of the prefix launch it would otherwise use, on a 152-SM
+// GB300.  Cells of 257..1,024 voxels: one per warp in the prefix layout fit
+// 14 per SM (2,128 cells); cells of 65..256 voxels: two per warp, 40 per SM
+// (6,080 cells).
+constexpr uint64_t kRecCellsLarge = 2128;
+constexpr uint64_t kRecCellsMid = 6080;
 tissue_launch default_launch(uint32_t V, uint64_t cells);
 // The default among prefix-layout launches (the fallback of a counts-only
 // launch that cannot take a tissue's model).

@@ -156,17 +156,22 @@ tissue_launch tsg::prefix_launch(uint32_t V, uint64_t cells) {
 }
 
 tissue_launch tsg::default_launch(uint32_t V, uint64_t cells) {
-  // Cells of more than 256 voxels in launches of many waves: two cells per
-  // warp in the counts-only layout (16-bit counts, 6.4 KB per cell: 32 cells
-  // per SM against 14 with the prefix layout), each event recomputing one
-  // sub-block of the selected block, one voxel per lane.  Same-box A/B,
-  // 256x256 cells of 32x32 voxels: 876 ms per chi step with the prefix
-  // layout, 542 ms with this one.  Fewer cells than about two waves of it
-  // keep one cell per warp, whose event chain is shorter.  Launches the
-  // counts-only layout cannot take (the promoter model, a trace) run
-  // prefix_launch.
-  if (V > 256 && V <= 1024 && cells >= kManyCells)
+  // Past one wave of the prefix launch, the counts-only layout, each event
+  // recomputing one sub-block of the selected block (one voxel per lane):
+  // - cells of 257..1,024 voxels two per warp (16-bit counts, 6.4 KB per
+  //   cell: 32 per SM against 14 in the prefix layout);
+  // - cells of 65..256 voxels four per warp (64 per SM against 40).
+  // Same-box A/B, chi ms per step (prefix launch -> this one): 32x32-voxel
+  // cells 25.8 -> 32.4 at 1,024 cells (one prefix wave: kept), 50.8 -> 36.5
+  // at 2,304, 68.5 -> 51.4 at 4,096, 876 -> 542 at 65,536; 16x16-voxel cells
+  // 9.4 -> 10.1 at 4,096 (kept), 18.8 -> 14.1 at 9,216, 32.0 -> 25.3 at
+  // 16,384.  Smaller launches keep the prefix layout, whose event chains are
+  // shorter.  Launches the counts-only layout cannot take (the promoter
+  // model, a trace) run prefix_launch.
+  if (V > 256 && V <= 1024 && cells > kRecCellsLarge)
     return tissue_launch{TISSUE_KERNEL_PERSISTENT, 16, 2, 0, TISSUE_LAYOUT_RECOMPUTE};
+  if (V > 64 && V <= 256 && cells > kRecCellsMid)
+    return tissue_launch{TISSUE_KERNEL_PERSISTENT, 8, 2, 0, TISSUE_LAYOUT_RECOMPUTE};
   return prefix_launch(V, cells);
 }
 

@@ -8,7 +8,7 @@ namespace tsg {
 
 ChiSegKernel chi_seg_kernel_narrow(int H, bool pre, bool qb) {
   // V > 256 makes B > H for 8 and 16 lanes; 32 lanes cover V <= 1024 with B <= H.
-  // The recompute layout: 32 lanes, or 16 lanes with up to four voxels per lane.
+  // The recompute layout: 32 lanes, or 16 lanes with up to four sub-blocks per block.
   if (!pre) {
     if (H == 32) return qb ? nullptr : k_chi_seg<32, false, false, 0, true>;
     if (H == 16) return qb ? k_chi_seg<16, false, true, 0, true> : nullptr;

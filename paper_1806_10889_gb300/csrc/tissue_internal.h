@@ -128,12 +128,14 @@ ChiSegKernel chi_seg_kernel_nd(int H, bool pre, bool qb);   // k_chi_seg.cu
 ChiSegKernel chi_seg_kernel_gen(int H, bool pre, bool qb);  // k_chi_seg_gen.cu
 ChiSegKernel chi_seg_kernel_pm(int H, bool pre, bool qb);   // k_chi_seg_pm.cu
 // 16-bit counts, Notch-Delta only (prefix layout at 8, 16 or 32 lanes; the
-// counts-only layout at 32 lanes); nullptr where not built.
+// counts-only layout at 32 lanes, or at 16 with sub-blocks); nullptr where
+// not built.
 ChiSegKernel chi_seg_kernel_narrow(int H, bool pre, bool qb);  // k_chi_seg_narrow.cu
 uint32_t seg_bytes_for(uint32_t V, int H, bool pre, bool narrow = false);
 // Whether the counts-only (recompute) layout takes cells of V voxels with H
 // lanes for launches of model code gen (k_chi_seg.cu): V <= H^2, or for the
-// Notch-Delta model (gen 0) up to four voxels per lane.
+// Notch-Delta model (gen 0) blocks of up to four sub-blocks of H voxels
+// (V <= 4 H^2 at 8 or 16 lanes).
 bool recompute_covers(uint32_t V, int H, int gen);
 // Well-mixed cells (k_chi_wm.cu): one warp per (tissue, cell) item;
 // vmax_cells is the largest V among the listed cells.

@@ -12,12 +12,20 @@
 // different size share one launch without idle warps.
 //
 // Per segment, shared memory holds a copy of its tissue's view (model,
-// pointers), the within-block prefix pre[] and the counts cnt[][] as in the
-// one-warp kernel.  Lane l of a segment owns voxels l*B .. l*B+B-1 (B a power
-// of two, H*B >= V).  The channel of the selected voxel is found without a
-// scan: lane j evaluates the running sum C_j of channels 0..j in closed form
-// (hop channels enter through the count of existing neighbour directions);
-// with H = 16, C_16..C_18 follow from C_15 by three additions.
+// pointers) and the counts cnt[][], and in the prefix layout the
+// within-block prefix pre[] as in the one-warp kernel.  Lane l of a segment
+// owns voxels l*B .. l*B+B-1 (B a power of two, H*B >= V) and keeps the
+// inclusive prefix P of the block totals in a register; selection takes a
+// block by one ballot over P, then a voxel inside it: from pre[] (prefix
+// layout), or by recomputing the block's voxel totals, one voxel per lane,
+// and scanning them (counts-only layout).  When a block is wider than the
+// segment (B > H) the counts-only layout first picks one of the block's
+// sub-blocks of H voxels from the running sums its owning lane keeps in
+// registers, and recomputes only that sub-block.  The channel of the
+// selected voxel is found without a scan: lane j evaluates the running sum
+// C_j of channels 0..j in closed form (hop channels enter through the count
+// of existing neighbour directions); with H = 16, C_16..C_18 follow from
+// C_15 by three additions.
 //
 // Both single-cell models share the 19 channel slots.  Per voxel a model
 // contributes three terms -- c0 (slot 0), c1 (slot 1) and the bimolecular

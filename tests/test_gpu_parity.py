@@ -380,3 +380,29 @@ def test_counts_only_layout_with_several_voxels_per_lane(lanes, n, wpb):
     bit-exact with the oracle."""
     spec = TissueSpec(3, 3, n, seed=300 + n, tissue_id=wpb).with_model(**STRONG)
     _run_both(spec, 0.1, 3, config=(T.KERNEL_PERSISTENT, lanes, wpb, 0, T.LAYOUT_RECOMPUTE))
+
+
+P_, R_ = T.LAYOUT_PREFIX, T.LAYOUT_RECOMPUTE
+
+
+@pytest.mark.parametrize("side,n,want", [
+    (16, 32, (T.KERNEL_PERSISTENT, 32, 2, 0, P_)),   # 256 cells: the machine is not full
+    (46, 32, (T.KERNEL_PERSISTENT, 32, 2, 0, P_)),   # 2,116 cells: one prefix wave
+    (47, 32, (T.KERNEL_PERSISTENT, 16, 2, 0, R_)),   # 2,209 cells: counts only
+    (77, 16, (T.KERNEL_PERSISTENT, 16, 4, 0, P_)),   # 5,929 cells: one prefix wave
+    (78, 16, (T.KERNEL_PERSISTENT, 8, 2, 0, R_)),    # 6,084 cells: counts only
+    (128, 8, (T.KERNEL_PERSISTENT, 8, 4, 0, P_)),    # 8x8-voxel cells keep the prefix layout
+])
+def test_default_launch_by_cell_size_and_count(side, n, want):
+    """The default launch takes the counts-only layout past one wave of the
+    prefix launch (2,128 cells of 257..1,024 voxels, 6,080 of 65..256)."""
+    g = Tissue(TissueSpec(side, side, n, seed=1))
+    assert g.launch_config() == want
+    g.close()
+
+
+@pytest.mark.parametrize("side,n", [(47, 32), (78, 16)])
+def test_default_counts_only_launch_matches_oracle(side, n):
+    """Whole tissues just past the thresholds, on their default (counts-only)
+    launch, every step bit-exact with the oracle."""
+    _run_both(TissueSpec(side, side, n, seed=40 + n, tissue_id=side), 0.1, 2)

@@ -48,10 +48,11 @@ def test_instruction_counts_were_measured_on_the_current_kernel():
     assert bench.CHI_IPE["sources"] == bench.chi_sources_sha(), (
         "the persistent chi kernel changed since its instructions per event were measured: "
         "re-run the ncu commands in profiles/k_chi_inst_per_event_by_cell_size.md")
-    # the default launches of the benchmark's workloads
-    for key in ("batch:V1024/H16/rec/qb1/nd/u16", "batch:V256/H16/pre/qb0/nd/u32",
-                "batch:V64/H8/pre/qb0/nd/u32", "medium:V256/H16/pre/qb0/nd/u32",
-                "large:V1024/H16/rec/qb1/nd/u16"):
+    # the default launches of the benchmark's workloads (the batch's 16x16-voxel
+    # class: 8 lanes, counts only, above 6,080 cells) and the former default
+    for key in ("batch:V1024/H16/rec/qb1/nd/u16", "batch:V256/H8/rec/qb1/nd/u32",
+                "batch:V256/H16/pre/qb0/nd/u32", "batch:V64/H8/pre/qb0/nd/u32",
+                "medium:V256/H16/pre/qb0/nd/u32", "large:V1024/H16/rec/qb1/nd/u16"):
         ipe, bpe = bench.CHI_IPE["kernels"][key]
         assert 100 < ipe < 1000 and 0 < bpe < 10
 
